@@ -1,0 +1,393 @@
+"""Pins of the CPU oracle against things other than itself: a hand-worked
+example, closed forms, brute-force recomputation, exact Eq. 5 probabilities,
+an independent Philox implementation (cuRAND's host generator) and the
+published Philox known-answer vectors. No GPU needed."""
+
+import ctypes
+import glob
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_24408_gb300 import instances as G
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _hand3():
+    D = F = None
+    perms = []
+    with open(os.path.join(GOLDEN, "qap3_hand.txt")) as fh:
+        for line in fh:
+            tok = line.split()
+            if not tok or tok[0].startswith("#"):
+                continue
+            if tok[0] == "D":
+                D = np.array(tok[1:], dtype=np.int32).reshape(3, 3)
+            elif tok[0] == "F":
+                F = np.array(tok[1:], dtype=np.int32).reshape(3, 3)
+            elif tok[0] == "P":
+                perms.append((tuple(int(t) for t in tok[1:4]), int(tok[4])))
+    return D, F, perms
+
+
+# --- Eq. 1 -------------------------------------------------------------------
+
+def test_cost_hand_worked_example():
+    D, F, perms = _hand3()
+    assert len(perms) == 6
+    for p, e in perms:
+        assert O.cost(D, F, p) == e
+
+
+def test_cost_closed_forms():
+    n = 7
+    F = G.random_symmetric(n, 0, 50, seed=3, tag=1, diag=True)
+    # D = all ones off the diagonal: every permutation costs the off-diagonal sum of F.
+    D = np.ones((n, n), np.int32) - np.eye(n, dtype=np.int32)
+    off = int(F.sum() - np.trace(F))
+    for rep in range(5):
+        p = O.init_perm(n, 11, 0, rep)
+        assert O.cost(D, F, p) == off
+    # D = identity: only the diagonal of F, permuted, which sums to trace(F).
+    Dd = np.eye(n, dtype=np.int32)
+    assert O.cost(Dd, F, O.init_perm(n, 5, 0, 0)) == int(np.trace(F))
+
+
+def test_brute_force_hand_and_closed_form():
+    D, F, perms = _hand3()
+    best, p, cnt = O.brute_force(D, F)
+    assert best == 32 and tuple(p) == (2, 1, 0) and cnt == 1
+    n = 6
+    Dc = np.ones((n, n), np.int32) - np.eye(n, dtype=np.int32)
+    Fc = G.dense_symmetric(n, 1, 9, 4, 2)
+    best, _, cnt = O.brute_force(Dc, Fc)
+    assert cnt == math.factorial(n) and best == int(Fc.sum())
+
+
+# --- Eq. 2 / Eq. 3 -----------------------------------------------------------
+
+@pytest.mark.parametrize("diag", [False, True])
+def test_influence_relations(diag):
+    n = 9
+    D = G.random_symmetric(n, -20, 40, seed=1, tag=3, diag=diag)
+    F = G.random_symmetric(n, -5, 30, seed=2, tag=5, diag=diag)
+    for rep in range(4):
+        p = O.init_perm(n, 99, 0, rep)
+        I = O.influence(D, F, p)
+        # E = sum_m I[m][p(m)] (Eq. 1 regrouped by location)
+        assert int(I[np.arange(n), p].sum()) == O.cost(D, F, p)
+        # Eq. 2 taken literally equals -2 x the stored one-term form (symmetric D, F)
+        assert np.array_equal(O.influence_eq2(D, F, p), -2 * I)
+
+
+@pytest.mark.parametrize("diag,lo", [(False, 0), (True, 0), (True, -30)])
+def test_delta_e_equals_brute_recomputation(diag, lo):
+    n = 8
+    D = G.random_symmetric(n, lo, 40, seed=7, tag=3, diag=diag)
+    F = G.random_symmetric(n, lo, 25, seed=8, tag=5, diag=diag)
+    for rep in range(6):
+        p = O.init_perm(n, 5, 1, rep)
+        I = O.influence(D, F, p)
+        e0 = O.cost(D, F, p)
+        for i in range(n):
+            for j in range(n):
+                q = p.copy()
+                q[i], q[j] = p[j], p[i]
+                assert O.delta_e(D, F, p, I, i, j) == O.cost(D, F, q) - e0
+
+
+def test_eq4_shortcut_is_not_exact():
+    """The Eq. 4 shortcut (drop the D x F correction of Eq. 3) misses 4 D_ij F_ab
+    on zero-diagonal symmetric instances; the oracle must not use it."""
+    D, F = G.named("n12")
+    n = 12
+    p = O.init_perm(n, 0, 0, 0)
+    I = O.influence(D, F, p)
+    wrong = 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            a, b = p[i], p[j]
+            eq4 = 2 * (I[i, b] - I[i, a] + I[j, a] - I[j, b])
+            exact = O.delta_e(D, F, p, I, i, j)
+            assert exact - eq4 == 4 * int(D[i, j]) * int(F[a, b])
+            wrong += exact != eq4
+    assert wrong > 0
+
+
+# --- Philox4x32-10 -----------------------------------------------------------
+
+def test_philox_known_answer_vectors():
+    # Known-answer vectors published with the Random123 library (Salmon et al., SC'11).
+    kat = [
+        ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+        ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+        ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+         [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+    ]
+    for ctr, key, want in kat:
+        assert list(O.philox4x32_10(ctr, key)) == want
+
+
+def _curand():
+    paths = glob.glob("/usr/local/cuda/lib64/libcurand.so*") + \
+        glob.glob("/usr/local/cuda/targets/*/lib/libcurand.so*")
+    for p in paths:
+        try:
+            return ctypes.CDLL(p)
+        except OSError:
+            continue
+    return None
+
+
+def test_philox_matches_curand_host_generator():
+    """cuRAND's host-side PHILOX4_32_10 generator (called, not re-typed) emits
+    block q of a seed as Philox(counter = (q / 65536, 0, q % 65536, 0), key = seed),
+    so it exercises counter words 0 and 2 and both key words; words 1 and 3
+    are covered by the known-answer vectors above."""
+    L = _curand()
+    if L is None:
+        pytest.skip("libcurand not found")
+    g = ctypes.c_void_p()
+    if L.curandCreateGeneratorHost(ctypes.byref(g), 161) != 0:
+        pytest.skip("cuRAND host generator unavailable")
+    try:
+        for seed, block0 in [(0, 0), (12345, 3), (0x0123456789ABCDEF, 65530), (2**64 - 1, 2**31 + 7)]:
+            assert L.curandSetPseudoRandomGeneratorSeed(g, ctypes.c_ulonglong(seed)) == 0
+            assert L.curandSetGeneratorOffset(g, ctypes.c_ulonglong(4 * block0)) == 0
+            nblk = 8
+            out = np.zeros(4 * nblk, np.uint32)
+            assert L.curandGenerate(g, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(out.size)) == 0
+            key = [seed & 0xFFFFFFFF, seed >> 32]
+            for q in range(nblk):
+                c = block0 + q
+                want = O.philox4x32_10([c >> 16, 0, c & 0xFFFF, 0], key)
+                assert np.array_equal(out[4 * q:4 * q + 4], want), (seed, c)
+    finally:
+        L.curandDestroyGenerator(g)
+
+
+def test_init_perm_is_uniform_permutation():
+    n = 4
+    counts = {}
+    R = 24000
+    for rep in range(R):
+        p = O.init_perm(n, 2024, 3, rep)
+        assert sorted(p) == list(range(n))
+        counts[tuple(p)] = counts.get(tuple(p), 0) + 1
+    assert len(counts) == 24
+    exp = R / 24
+    chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
+    # 23 degrees of freedom; P(chi2 > 60) < 1e-4
+    assert chi2 < 60
+
+
+# --- The fp32 weights of Eq. 5 -----------------------------------------------
+
+def test_expneg_f32_accuracy_and_shape():
+    xs = np.concatenate([np.linspace(0, 40, 20001, dtype=np.float32),
+                         np.float32([1e-30, 1e-7, 0.34657359, 0.34657362, 20.5, 39.9999])])
+    worst = 0.0
+    prev = None
+    for x in np.sort(xs):
+        got = float(O.expneg_f32(x))
+        ref = math.exp(-float(x))
+        worst = max(worst, abs(got - ref) / ref)
+        if prev is not None:
+            assert got <= prev
+        prev = got
+    assert float(O.expneg_f32(0.0)) == 1.0
+    # within 3 units in the last place of binary32
+    assert worst < 3 * 2.0 ** -24, worst
+
+
+def test_weight_quantisation():
+    assert O.weight(0.0) == 2 ** 53
+    assert O.weight(40.5) == 0 and O.weight(1e30) == 0
+    for x in [0.25, 1.0, 5.0, 17.0, 30.0]:
+        e = float(O.expneg_f32(x))
+        assert O.weight(x) == math.floor(e * 2.0 ** 53)
+
+
+def _exact_probs(dE, beta):
+    z = np.exp(-np.float64(np.float32(beta)) * (dE - dE.min()).astype(np.float64))
+    return z / z.sum()
+
+
+@pytest.mark.parametrize("name,beta", [("n12", 0.05), ("n12", 0.5), ("n30", 0.02), ("n30", 0.2)])
+def test_sampler_probabilities_within_1e6_of_eq5(name, beta):
+    D, F = G.named(name)
+    n = D.shape[0]
+    for rep in range(3):
+        p = O.init_perm(n, 1, 0, rep)
+        for i in range(0, n, 3):
+            _, dE, w, _ = O.choose(D, F, p, i, beta, 12345)
+            exact = _exact_probs(dE, beta)
+            q = w.astype(np.float64) / float(w.astype(np.float64).sum())
+            big = exact >= 1e-9
+            rel = np.abs(q[big] - exact[big]) / exact[big]
+            assert rel.max() < 1e-6
+            assert np.abs(q[~big] - exact[~big]).max(initial=0.0) < 1e-12
+            assert dE[i] == 0
+
+
+def test_sampler_beta_zero_is_uniform_closed_form():
+    D, F = G.named("n12")
+    n = 12
+    p = O.init_perm(n, 3, 0, 0)
+    for k in range(40):
+        r = O.update_draw(9, 0, 0, k, 5)
+        j, _, w, _ = O.choose(D, F, p, 5, 0.0, r)
+        assert all(int(x) == 2 ** 53 for x in w)
+        assert j == (r * n) >> 64
+
+
+def test_sampler_large_beta_is_argmin():
+    D, F = G.named("n30")
+    n = 30
+    for rep in range(5):
+        p = O.init_perm(n, 4, 0, rep)
+        for i in range(0, n, 4):
+            j, dE, w, _ = O.choose(D, F, p, i, 1e30, O.update_draw(1, 0, rep, 0, i))
+            mins = np.flatnonzero(dE == dE.min())
+            assert j in mins
+            assert all(int(w[k]) == (2 ** 53 if k in mins else 0) for k in range(n))
+
+
+def test_one_step_law_chi_square():
+    """Frequencies of one update's outcome over many Philox draws against exact
+    Eq. 5 probabilities (N = 5, fixed state)."""
+    n = 5
+    D = G.random_symmetric(n, 0, 9, seed=5, tag=9)
+    F = G.random_symmetric(n, 0, 9, seed=6, tag=9)
+    p = O.init_perm(n, 7, 0, 0)
+    beta, i = 0.15, 2
+    _, dE, _, _ = O.choose(D, F, p, i, beta, 0)
+    probs = _exact_probs(dE, beta)
+    draws = 60000
+    counts = np.zeros(n)
+    for s in range(draws):
+        j, _, _, _ = O.choose(D, F, p, i, beta, O.update_draw(77, 0, 0, s, i))
+        counts[j] += 1
+    exp = probs * draws
+    keep = exp > 5
+    chi2 = float(((counts[keep] - exp[keep]) ** 2 / exp[keep]).sum())
+    # <= 4 degrees of freedom: P(chi2 > 23.5) < 1e-4
+    assert chi2 < 23.5, (counts, exp)
+
+
+# --- Whole runs: invariants and brute-force optima ----------------------------
+
+def test_anneal_invariants_and_incremental_tables():
+    D, F = G.named("n30")
+    n = 30
+    beta = O.beta_schedule("geometric", 60, O.beta_max(D, F))
+    r = O.anneal(D, F, beta, 60, seed=3, rep_begin=5, rep_end=9, tables=True)
+    for k in range(4):
+        fp, bp = r["final_perm"][k], r["best_perm"][k]
+        assert sorted(fp) == list(range(n)) and sorted(bp) == list(range(n))
+        assert r["final_cost"][k] == O.cost(D, F, fp)
+        assert r["best_cost"][k] == O.cost(D, F, bp)
+        assert r["best_cost"][k] <= r["final_cost"][k]
+        assert np.array_equal(r["tables"][k], O.influence(D, F, fp))
+        assert r["accepted"][k] > 0
+
+
+def test_anneal_zero_sweeps_returns_initial_state():
+    D, F = G.named("n12")
+    r = O.anneal(D, F, np.zeros(1, np.float32), 0, seed=1, rep_begin=0, rep_end=3)
+    for k in range(3):
+        p0 = O.init_perm(12, 1, 0, k)
+        assert np.array_equal(r["best_perm"][k], p0)
+        assert r["best_cost"][k] == O.cost(D, F, p0) and r["best_sweep"][k] == -1
+
+
+def test_anneal_reaches_brute_force_optimum_n9():
+    D, F = G.named("n9")
+    best, _, _ = O.brute_force(D, F)
+    beta = O.beta_schedule("linear", 1000, O.beta_max(D, F))
+    r = O.anneal(D, F, beta, 1000, seed=0, rep_begin=0, rep_end=64, threads=4)
+    assert r["cost"] == best
+    assert O.cost(D, F, r["perm"]) == best
+    assert (r["best_cost"] >= best).all()
+
+
+def test_anneal_n12_optimum_matches_stored_brute_force():
+    """The 12! brute-force optimum of the 3x4-grid instance is stored by
+    tests/golden/make_golden.py (which calls only the oracle)."""
+    with open(os.path.join(GOLDEN, "n12_optimum.txt")) as fh:
+        vals = dict(line.split() for line in fh if line.strip() and not line.startswith("#"))
+    D, F = G.named("n12")
+    opt = int(vals["optimum"])
+    p = np.array(vals["perm"].split(","), dtype=np.int32)
+    assert O.cost(D, F, p) == opt
+    beta = O.beta_schedule("linear", 1000, O.beta_max(D, F))
+    r = O.anneal(D, F, beta, 1000, seed=0, rep_begin=0, rep_end=64, threads=4)
+    assert r["cost"] == opt
+
+
+def test_threads_do_not_change_results():
+    D, F = G.named("n12")
+    beta = O.beta_schedule("linear", 50, O.beta_max(D, F))
+    a = O.anneal(D, F, beta, 50, seed=8, rep_begin=0, rep_end=8, threads=1)
+    b = O.anneal(D, F, beta, 50, seed=8, rep_begin=0, rep_end=8, threads=3)
+    c = O.anneal(D, F, beta, 50, seed=8, rep_begin=4, rep_end=8, threads=1)
+    for key in ["final_perm", "best_cost", "best_sweep", "accepted"]:
+        assert np.array_equal(a[key], b[key])
+        assert np.array_equal(a[key][4:], c[key])
+
+
+# --- Parallel tempering exchange ---------------------------------------------
+
+def test_pt_exchange_hand_cases():
+    # rung_of_slot = identity. Energies decreasing with beta: nothing moves.
+    rung, c = O.pt_exchange([10, 8, 6, 4], [0, 1, 2, 3], 0, 100)
+    assert list(rung) == [0, 1, 2, 3] and c == 1
+    # The coldest configuration sits at the hottest rung: it bubbles to the top
+    # in one ascending pass (ties also move up).
+    rung, c = O.pt_exchange([4, 6, 8, 10], [0, 1, 2, 3], 7, 100)
+    assert list(rung) == [3, 0, 1, 2] and c == 0
+    rung, c = O.pt_exchange([5, 5, 5], [2, 0, 1], 0, 100)
+    # slot1 at rung0, slot2 at rung1, slot0 at rung2; ties swap: slot1 climbs to the top.
+    assert list(rung) == [1, 2, 0] and c == 0
+    # Timeout: the top rung took no part for `timeout` periods -> top <-> bottom.
+    rung, c = O.pt_exchange([10, 8, 6, 4], [0, 1, 2, 3], 99, 100)
+    assert list(rung) == [3, 1, 2, 0] and c == 0
+
+
+def test_pt_anneal_invariants():
+    D, F = G.named("n12")
+    bm = O.beta_max(D, F)
+    ladder = np.float32([bm * 0.05 * (20.0 ** (q / 4)) for q in range(5)])
+    r = O.anneal(D, F, ladder, 40, seed=2, rep_begin=0, rep_end=10, mode="pt", ladder_len=5,
+                 period=4, timeout=3)
+    for g in range(2):
+        assert sorted(r["rung"][5 * g:5 * g + 5]) == list(range(5))
+    for k in range(10):
+        assert r["best_cost"][k] == O.cost(D, F, r["best_perm"][k])
+        assert r["final_cost"][k] == O.cost(D, F, r["final_perm"][k])
+
+
+# --- Beta schedules ------------------------------------------------------------
+
+def test_beta_schedules():
+    b = O.beta_schedule("linear", 11, 2.0)
+    assert b[0] == 0.0 and b[-1] == np.float32(2.0) and np.all(np.diff(b) > 0)
+    g = O.beta_schedule("geometric", 7, 3.0)
+    assert g[0] == np.float32(0.003) and g[-1] == np.float32(3.0)
+    assert np.allclose(g[1:] / g[:-1], 1000 ** (1 / 6), rtol=1e-6)
+    D, F = G.named("n12")
+    n = 12
+    p = np.arange(n, dtype=np.int32)
+    pos = []
+    for i, j in itertools.combinations(range(n), 2):
+        q = p.copy()
+        q[i], q[j] = j, i
+        d = O.cost(D, F, q) - O.cost(D, F, p)
+        if d > 0:
+            pos.append(d)
+    assert O.beta_max(D, F) == pytest.approx(10.0 / np.mean(pos), rel=1e-12)
