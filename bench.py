@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the annealed p-dit sweep (one JSON line on stdout).
+
+Workload (default): dense symmetric QAP, N = 100, D and F off-diagonal entries
+uniform in 0..99 (seeded, synthetic), 4096 replicas, 10000 sweeps, linear
+beta schedule 0 -> beta_max. One step = one complete anneal of that workload
+through the C ABI: Fisher-Yates initial permutations, influence tables,
+10000 sweeps, best-so-far tracking and the final reduction to the best
+permutation. Metric: p-dit updates per second (one update = one location's
+Eq. 5 draw; N x replicas x sweeps per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1: one process per GPU (torchrun); rank r runs replicas r*R..(r+1)*R-1
+(weak scaling, no collective in the timed region); value = all ranks'
+updates / max-over-ranks time.
+--impl reference: the CPU oracle on this host's cores (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_24408_gb300 import instances as G  # noqa: E402
+
+WORKLOADS = {
+    # name: (instance, replicas, sweeps, schedule)
+    "n100": ("n100", 4096, 10000, "linear"),
+    "n30": ("n30", 1024, 5000, "geometric"),
+    "n12": ("n12", 64, 1000, "linear"),
+}
+METRIC = "p-dit updates/s"
+L2_FLUSH_BYTES = 512 << 20
+SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM per clock (32 banks x 4 B)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_kernel_n100_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_24408_gb300", "csrc", f)
+                  for f in ("pdit_sweep.cuh", "pdit_host.cu")]
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float) -> float:
+    """Shared-memory bytes one update must move in this design.
+    Gather (every update): p[j], I[i][p(j)], I[j][p(i)], h[j] as int32, plus
+    D[i][j] and F[p(i)][p(j)] at the staged width: 16 N + 2 N dt.
+    Accepted swap: read+write of the N x N int32 table (8 N^2), the two F
+    rows and two D rows (4 N dt), the column factor written once (4 N) and
+    the p-diagonal gathered and rewritten (8 N)."""
+    gather = 16 * n + 2 * n * dt_bytes
+    swap = 8 * n * n + 4 * n * dt_bytes + 12 * n
+    return gather + accept_frac * swap
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(D, F, beta, n: int, sweeps: int) -> dict:
+    """The CPU oracle as it stands, one replica per host core over the full
+    schedule (a bounded sample of the workload's replicas)."""
+    import oracle as O
+
+    cores = host_cores()
+    t = time.perf_counter()
+    O.anneal(D, F, beta, sweeps, 0, 0, cores, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": cores * n * sweeps / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": "%d of the replicas (ids 0..%d), all %d sweeps, one per core; %.1f s"
+                      % (cores, cores - 1, sweeps, dt)}
+
+
+def run_reference(args, wl):
+    """--impl reference: the CPU oracle on this host, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+
+    inst, replicas, sweeps, kind = WORKLOADS[wl]
+    D, F = G.named(inst)
+    n = D.shape[0]
+    beta_full = O.beta_schedule(kind, sweeps, O.beta_max(D, F))
+    sub = max(1, sweeps // 1000)
+    beta = np.ascontiguousarray(beta_full[::sub])
+    s_steps = len(beta)
+    cores = host_cores()
+    upd = cores * n * s_steps
+
+    def step(k):
+        O.anneal(D, F, beta, s_steps, 1000 + k, 0, cores, threads=cores)
+
+    for k in range(args.warmup):
+        step(k)
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        step(args.warmup + k)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    value = upd * args.steps / tot
+    sample = ("per step: %d replicas (one per core) x %d sweeps, the %d-sweep schedule taken every "
+              "%d-th sweep (same beta range)" % (cores, s_steps, sweeps, sub))
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "%s: N=%d, %d replicas x %d sweeps, %s beta" % (wl, n, replicas, sweeps, kind),
+                       "global_batch": replicas, "seq_len": n, "parallelism": "cpu threads",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+
+    import torch
+
+    from paper_2605_24408_gb300 import build as B
+    from paper_2605_24408_gb300 import pdit as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+
+    inst, replicas, sweeps, kind = WORKLOADS[args.workload]
+    D, F = G.named(inst)
+    n = D.shape[0]
+    q = P.Qap(D, F)
+    beta = P.pdit_beta_schedule(kind, sweeps, P.pdit_beta_max(q))
+    dev = torch.device("cuda", local)
+    dbeta = torch.from_numpy(beta).to(dev)
+    base = rank * replicas
+    stream = torch.cuda.current_stream(dev)
+    outs = {"best_perm": torch.empty(n, dtype=torch.int32, device=dev),
+            "best_cost": torch.empty(1, dtype=torch.int64, device=dev),
+            "replica_accepted": torch.empty(replicas, dtype=torch.int64, device=dev),
+            "status": torch.zeros(1, dtype=torch.int32, device=dev)}
+    o = P.opts(replicas=replicas, sweeps=sweeps, seed=0, replica_base=base, beta=dbeta.data_ptr(),
+               stream=stream.cuda_stream)
+    ws = torch.empty(P.pdit_workspace_bytes(q, o), dtype=torch.uint8, device=dev)
+    o.workspace, o.workspace_bytes = ws.data_ptr(), ws.numel()
+    for k, t in outs.items():
+        setattr(o, k, t.data_ptr())
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        P.pdit_anneal_ex(q, o)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (outside the events)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    status = int(outs["status"].item())
+    if status != 0:
+        raise SystemExit("device audit failed: status %d" % status)
+    upd_rank = n * replicas * sweeps
+    value = world * upd_rank * args.steps / (tot_ms / 1000.0)
+    accepted = int(outs["replica_accepted"].sum().item())
+    accept_frac = accepted / upd_rank
+
+    # final answer over ranks (outside the timed region)
+    best_cost = int(outs["best_cost"].item())
+    if dist is not None:
+        from paper_2605_24408_gb300 import multi
+
+        best_cost, _, _ = multi.global_best(best_cost, 0, outs["best_perm"].cpu().numpy(), base, dev)
+
+    # end to end: host buffers through pdit_anneal (H2D of beta, D2H of the result per step)
+    hbeta = torch.from_numpy(beta).pin_memory()
+    hperm = torch.empty(n, dtype=torch.int32).pin_memory()
+    hcost = torch.empty(1, dtype=torch.int64).pin_memory()
+    e2e_t = []
+    for k in range(args.e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = P.pdit_anneal_host_ptrs(q, replicas, hbeta.data_ptr(), sweeps, 0, hperm.data_ptr(),
+                                     hcost.data_ptr())
+        t1 = time.perf_counter()
+        if rc != 0:
+            raise SystemExit("pdit_anneal failed: %s" % P.strerror(rc))
+        if k > 0:  # the first call allocates the handle's buffers
+            e2e_t.append(t1 - t0)
+    e2e_val = world * upd_rank * len(e2e_t) / sum(e2e_t)
+    assert int(hcost[0]) == int(outs["best_cost"].item()) or dist is not None
+
+    # roofline of the sweep kernel: shared-memory bound
+    props = torch.cuda.get_device_properties(dev)
+    dt_bytes = 1 if max(abs(int(D.max())), abs(int(F.max()))) <= 127 else 2
+    bpu = algorithmic_bytes_per_update(n, dt_bytes, accept_frac)
+    kernel_s = tot_ms / 1000.0 / args.steps
+    achieved = bpu * upd_rank / kernel_s / 1e9
+    sm_mhz = clk.get("sm_mhz") or 0.0
+    peak = props.multi_processor_count * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9 if sm_mhz else None
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        if tr.get("source_sha") == kernel_source_sha():
+            traffic = tr.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "%s: dense symmetric QAP N=%d (D, F uniform 0..99)" % (args.workload, n)
+                   if args.workload == "n100" else args.workload,
+                   "replicas_per_gpu": replicas, "sweeps": sweeps, "schedule": kind, "seed": 0,
+                   "global_batch": replicas * world, "seq_len": n,
+                   "parallelism": "replicas sharded over %d GPU(s)" % world,
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "accept_fraction": accept_frac, "best_cost": best_cost},
+        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 4 * sweeps,
+                "d2h_bytes_per_step": 4 * n + 8 + 4},
+        "gpu_launches": 2 * args.steps,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                   "reasons": clk.get("reasons"), "samples": clk.get("samples")},
+        "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if peak else None, "traffic": traffic,
+                     "kernel": "sweep_kernel<int8,4,smem>",
+                     "bytes_per_update": bpu,
+                     "peak_source": "derived: %d SMs x %d B/clk x median SM clock under load (%s MHz)"
+                                    % (props.multi_processor_count, SMEM_BYTES_PER_CLK, sm_mhz)},
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(D, F, beta, n, sweeps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    q.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

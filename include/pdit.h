@@ -1,0 +1,186 @@
+/*
+ * libpdit -- p-dit probabilistic Ising machine for the symmetric quadratic
+ * assignment problem, on NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2605.24408, "P-dit Probabilistic Ising Machine for Solving
+ * the Quadratic Assignment Problem". The QAP is min_p sum_ij D_ij F_{p(i)p(j)}
+ * (Eq. 1). Each location holds a p-dit whose state is the facility assigned
+ * to it. An update of location i chooses, with the Boltzmann law of Eq. 5,
+ * between staying and swapping facilities with one of the other N-1
+ * locations, using the exact swap energy of Eq. 3 computed from an influence
+ * table (Eq. 2) that is updated incrementally after every accepted swap. A
+ * sweep updates every location once, in index order. Plain mode anneals the
+ * inverse temperature beta along a per-sweep schedule; PT mode runs
+ * parallel tempering (Implementation section; CPU-PIM Algorithm section).
+ *
+ * Conventions for every call:
+ *  - Return 0 (PDIT_OK) on success, a negative PDIT_E* code on failure. No
+ *    C++ exception crosses this interface.
+ *  - Matrices are int32, row-major, N x N. Permutations are 0-based:
+ *    perm[i] = facility at location i. Costs are int64 and exact.
+ *  - Output buffers are owned by the caller. A handle is not thread-safe:
+ *    use one handle per host thread.
+ *  - Device work of pdit_anneal_ex is ordered on the caller's stream and is
+ *    asynchronous; pdit_anneal is synchronous.
+ *  - Results are a pure function of (D, F, beta values, seed, instance_id,
+ *    global replica id): independent of the GPU, the launch shape and how
+ *    replicas are split across calls.
+ */
+#ifndef PDIT_H
+#define PDIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define PDIT_OK 0
+#define PDIT_EINVAL (-1)  /* NULL pointer, size out of range, D or F not symmetric, bad beta */
+#define PDIT_ERANGE (-2)  /* 16 (N+2) max|D| max|F| >= 2^31: the int32 tables could overflow */
+#define PDIT_ENOMEM (-3)  /* an allocation failed, or the caller's workspace is too small */
+#define PDIT_ECUDA (-4)   /* a CUDA runtime call failed; see pdit_last_error() */
+#define PDIT_EDEVICE (-5) /* a device-side consistency audit failed (see PDIT_STATUS_*) */
+#define PDIT_ENOTSUP (-6) /* a valid request this build cannot run */
+
+/* Largest instance size. */
+#define PDIT_N_MAX 256
+
+/* Modes. */
+#define PDIT_MODE_ANNEAL 0 /* beta[s] for sweep s, every replica */
+#define PDIT_MODE_PT 1     /* parallel tempering over a beta ladder */
+
+/* Flags. */
+#define PDIT_FLAG_RESUME 1u /* continue from the replica state already in the workspace */
+
+/* Device status bits (opts.status). */
+#define PDIT_STATUS_ENERGY_AUDIT 1 /* tracked energy != energy recomputed from the table */
+
+typedef struct pdit_qap pdit_qap;
+
+/*
+ * qap_create -- upload one QAP instance (Eq. 1 inputs) to the current CUDA
+ * device.
+ *   n      : 2 <= n <= PDIT_N_MAX.
+ *   D, F   : host pointers, n*n int32 each, row-major; both must be
+ *            symmetric (the paper treats the symmetric QAP, Eq. 1). Any
+ *            diagonal and any sign are accepted. Copied; the caller keeps
+ *            ownership.
+ *   out    : receives the handle (owns device copies of D and F).
+ * Errors: PDIT_EINVAL (n out of range, NULL, asymmetric), PDIT_ERANGE
+ * (values too large for exact int32 table arithmetic), PDIT_ENOMEM,
+ * PDIT_ECUDA. On error *out is set to NULL.
+ */
+int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out);
+
+/* qap_destroy -- free the handle and its device memory. NULL-safe. */
+void qap_destroy(pdit_qap *h);
+
+/* qap_n -- the instance size of a handle, or PDIT_EINVAL for NULL. */
+int qap_n(const pdit_qap *h);
+
+/*
+ * pdit_anneal -- synchronous annealed p-dit sweep on HOST buffers.
+ *   replicas      : >= 1 independent chains (replica ids 0..replicas-1).
+ *   beta_schedule : host, `sweeps` floats, beta of sweep s (finite, >= 0).
+ *   sweeps        : >= 0 (0 returns the best initial permutation).
+ *   seed          : Philox key.
+ *   best_perm     : host, n int32: the best permutation over all replicas
+ *                   (smallest cost, ties to the lowest replica id).
+ *   best_cost     : host, its Eq. 1 cost.
+ * Copies beta to the device and the result back inside the call; uses a
+ * stream and a workspace owned by the handle.
+ * Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ECUDA, PDIT_EDEVICE.
+ */
+int pdit_anneal(pdit_qap *h, int replicas, const float *beta_schedule, int sweeps, uint64_t seed,
+                int32_t *best_perm, int64_t *best_cost);
+
+/*
+ * Options of pdit_anneal_ex. Initialise with pdit_opts_init, then set
+ * fields. Every pointer below is a DEVICE pointer on the handle's device.
+ */
+typedef struct pdit_opts {
+    uint32_t struct_size;   /* sizeof(pdit_opts); set by pdit_opts_init */
+    int replicas;           /* chains in this call, >= 1 */
+    int sweeps;             /* schedule length S (anneal mode: length of beta) */
+    int sweep_begin;        /* run sweeps [sweep_begin, sweep_end); default 0 */
+    int sweep_end;          /* default -1 = sweeps */
+    uint64_t seed;          /* Philox key */
+    uint32_t instance_id;   /* Philox counter word 0; default 0 */
+    uint32_t replica_base;  /* global id of this call's replica 0 (counter word 1); default 0 */
+    int mode;               /* PDIT_MODE_ANNEAL (default) or PDIT_MODE_PT */
+    const float *beta;      /* anneal: [sweeps]; PT: [ladder_len], rung 0 = smallest beta */
+    int ladder_len;         /* PT: replicas per set (2..64); replicas % ladder_len == 0 */
+    int exchange_period;    /* PT: sweeps between exchanges (paper: 4) */
+    int timeout_periods;    /* PT: periods without a top-rung swap before top<->bottom (paper: 100); 0 = off */
+    uint32_t flags;         /* PDIT_FLAG_* */
+    void *stream;           /* cudaStream_t; NULL = the legacy default stream */
+    void *workspace;        /* >= pdit_workspace_bytes(); NULL = owned by the handle (allocates) */
+    size_t workspace_bytes;
+    /* outputs; best_perm and best_cost are required, the rest optional (NULL) */
+    int32_t *best_perm;          /* [n] */
+    int64_t *best_cost;          /* [1] */
+    int64_t *replica_best_cost;  /* [replicas] */
+    int32_t *replica_best_perm;  /* [replicas * n] */
+    int32_t *replica_best_sweep; /* [replicas]; -1 = the initial state */
+    int32_t *replica_final_perm; /* [replicas * n] */
+    int64_t *replica_final_cost; /* [replicas] */
+    int64_t *replica_accepted;   /* [replicas]: accepted swaps in this call's sweeps (cumulative on resume) */
+    int32_t *replica_rung;       /* [replicas]: PT rung of each replica at the end */
+    int32_t *tables;             /* [replicas * n * n]: final influence tables I[m][c] */
+    int32_t *status;             /* [1]: PDIT_STATUS_* bits, 0 if every audit passed */
+} pdit_opts;
+
+/* pdit_opts_init -- defaults (see the field comments). NULL-safe. */
+void pdit_opts_init(pdit_opts *o);
+
+/*
+ * pdit_workspace_bytes -- device scratch needed by pdit_anneal_ex for the
+ * given options (replicas, mode, ladder). Returns 0 for invalid input.
+ * The workspace holds every replica's state between calls (permutation,
+ * energy, best-so-far, counters, and in PT mode the influence tables), so a
+ * call with PDIT_FLAG_RESUME continues exactly where the previous one
+ * stopped.
+ */
+size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o);
+
+/*
+ * pdit_anneal_ex -- asynchronous annealed p-dit sweep (or parallel
+ * tempering) on DEVICE buffers, ordered on o->stream.
+ * Without PDIT_FLAG_RESUME, replicas start from a Philox Fisher-Yates
+ * permutation. Sweeps [sweep_begin, sweep_end) run; beta comes from
+ * o->beta. The best over this call's replicas goes to best_perm/best_cost.
+ * Errors (host-detected, nothing launched): PDIT_EINVAL, PDIT_ENOMEM,
+ * PDIT_ECUDA. Device audits are reported through o->status.
+ */
+int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o);
+
+/*
+ * pdit_beta_max -- the default largest beta for an instance: 10 / (mean
+ * positive Eq. 3 swap energy over all n(n-1)/2 swaps from the identity
+ * permutation). A convention of this library; the paper selects its beta
+ * range by trial runs instead (Implementation section).
+ */
+int pdit_beta_max(const pdit_qap *h, double *beta_max);
+
+/*
+ * pdit_beta_schedule -- fill out[sweeps] on the host.
+ *   kind 0: linear, beta_s = beta_max * s / (sweeps - 1) (0 -> beta_max);
+ *   kind 1: geometric, beta_s = (beta_max/1000) * 1000^(s/(sweeps-1)).
+ * A single sweep gets beta_max. Errors: PDIT_EINVAL.
+ */
+int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out);
+
+/* pdit_strerror -- static text for an error code. */
+const char *pdit_strerror(int code);
+
+/* pdit_last_error -- text of the last CUDA failure on this host thread. */
+const char *pdit_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDIT_H */

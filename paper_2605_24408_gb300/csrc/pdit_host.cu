@@ -1,0 +1,565 @@
+// C ABI of libpdit (include/pdit.h): instance upload, launch planning,
+// parallel-tempering exchange, final reduction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pdit.h"
+#include "pdit_sweep.cuh"
+
+struct pdit_qap {
+    int n = 0;
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    int dt_bytes = 4;       // storage of D and F in shared memory: 1, 2 or 4 bytes
+    int zero_diag = 0;
+    std::vector<int32_t> hD, hF;
+    int32_t *dD = nullptr, *dF = nullptr;
+    // owned by the handle, grown on demand
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    float *dbeta = nullptr;
+    size_t dbeta_cap = 0;
+    int32_t *dperm = nullptr;
+    int64_t *dcost = nullptr;
+    int32_t *dstatus = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return PDIT_ECUDA;
+}
+
+#define PDIT_CK(call)                                            \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Smallest 4*odd >= n: rows start 16-byte aligned and a quarter-warp's
+// column-wise int4 accesses to 8 consecutive rows hit 8 disjoint bank groups.
+int table_stride(int n) {
+    int s = (n + 3) & ~3;
+    if ((s / 4) % 2 == 0) s += 4;
+    return s;
+}
+
+int maxk_for(int n) {
+    int k = (n + 31) / 32;
+    int p = 1;
+    while (p < k) p <<= 1;
+    return p;
+}
+
+int warp_cap(int maxk) { return maxk == 1 ? 32 : (maxk == 2 ? 16 : (maxk == 4 ? 12 : 4)); }
+
+struct Plan {
+    int maxk = 1;
+    bool tsmem = true;
+    int stride = 0;
+    size_t df_bytes = 0, warp_bytes = 0, smem = 0;
+    int warps = 1, threads = 32, grid = 1;
+};
+
+int sweep_blocks(int dt, int maxk, bool tsmem, int threads, size_t smem, int *blocks) {
+    if (dt == 1) return pdit::sweep_blocks_per_sm<int8_t>(maxk, tsmem, threads, smem, blocks);
+    if (dt == 2) return pdit::sweep_blocks_per_sm<int16_t>(maxk, tsmem, threads, smem, blocks);
+    return pdit::sweep_blocks_per_sm<int32_t>(maxk, tsmem, threads, smem, blocks);
+}
+
+int sweep_launch(int dt, int maxk, bool tsmem, const pdit::SweepArgs &a, int grid, int threads,
+                 size_t smem, cudaStream_t st) {
+    if (dt == 1) return pdit::sweep_launch<int8_t>(maxk, tsmem, a, grid, threads, smem, st);
+    if (dt == 2) return pdit::sweep_launch<int16_t>(maxk, tsmem, a, grid, threads, smem, st);
+    return pdit::sweep_launch<int32_t>(maxk, tsmem, a, grid, threads, smem, st);
+}
+
+// Launch shape for `replicas` chains of an n-location instance.
+int make_plan(const pdit_qap *h, int replicas, Plan *p) {
+    const int n = h->n;
+    p->maxk = maxk_for(n);
+    p->stride = table_stride(n);
+    const size_t npad = (size_t)((n + 3) & ~3);
+    const size_t svn = std::max((size_t)p->stride, (size_t)(32 * p->maxk));
+    p->df_bytes = align_up((size_t)2 * n * n * h->dt_bytes, 16);
+    const size_t vec_bytes = 4 * (2 * npad + svn);
+    const size_t table_bytes = (size_t)4 * n * p->stride;
+    const size_t budget = h->smem_optin;
+    size_t wb = align_up(table_bytes + vec_bytes, 16);
+    p->tsmem = p->df_bytes + wb <= budget;
+    if (!p->tsmem) {
+        if (p->maxk < 4) return PDIT_ENOTSUP;
+        wb = align_up(vec_bytes, 16);
+        if (p->df_bytes + wb > budget) return PDIT_ENOTSUP;
+    }
+    p->warp_bytes = wb;
+    int w = (int)((budget - p->df_bytes) / wb);
+    w = std::min(w, warp_cap(p->maxk));
+    const int per_sm = (replicas + h->num_sms - 1) / h->num_sms;
+    w = std::max(1, std::min(w, per_sm));
+    p->warps = w;
+    p->threads = 32 * w;
+    p->smem = p->df_bytes + (size_t)w * wb;
+    int bps = 0;
+    int e = sweep_blocks(h->dt_bytes, p->maxk, p->tsmem, p->threads, p->smem, &bps);
+    if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
+    if (bps < 1) bps = 1;
+    const int need = (replicas + w - 1) / w;
+    p->grid = std::max(1, std::min(need, h->num_sms * bps));
+    return PDIT_OK;
+}
+
+struct Workspace {
+    int32_t *perm, *best_perm, *best_sweep, *rung, *since_top, *queue, *status, *tables;
+    int64_t *energy, *best_energy, *accepted;
+    size_t bytes;
+};
+
+bool needs_tables(const pdit_opts *o, const Plan &p) { return o->mode == PDIT_MODE_PT || !p.tsmem; }
+
+Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base) {
+    const size_t R = (size_t)o->replicas, n = (size_t)h->n;
+    size_t off = 0;
+    Workspace w{};
+    auto take = [&](size_t bytes) {
+        char *ptr = base ? base + off : nullptr;
+        off = align_up(off + bytes, kAlign);
+        return ptr;
+    };
+    w.perm = (int32_t *)take(4 * R * n);
+    w.best_perm = (int32_t *)take(4 * R * n);
+    w.energy = (int64_t *)take(8 * R);
+    w.best_energy = (int64_t *)take(8 * R);
+    w.accepted = (int64_t *)take(8 * R);
+    w.best_sweep = (int32_t *)take(4 * R);
+    w.rung = (int32_t *)take(4 * R);
+    const size_t nsets = o->mode == PDIT_MODE_PT && o->ladder_len > 0 ? R / (size_t)o->ladder_len : 1;
+    w.since_top = (int32_t *)take(4 * nsets);
+    w.queue = (int32_t *)take(4 * 64);
+    w.status = (int32_t *)take(4);
+    w.tables = needs_tables(o, p) ? (int32_t *)take(4 * R * n * (size_t)p.stride) : nullptr;
+    w.bytes = off;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers: PT rung initialisation and exchange, final reduction.
+// ---------------------------------------------------------------------------
+__global__ void init_pt_kernel(int replicas, int ladder, int32_t *rung, int32_t *since_top,
+                               uint32_t rep_base) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < replicas) rung[r] = (int32_t)((rep_base + (uint32_t)r) % (uint32_t)ladder);
+    if (r < replicas / ladder) since_top[r] = 0;
+}
+
+// One thread per set of `ladder` consecutive replicas. Rungs ascend in beta.
+// For q = 0..L-2: if the replica at rung q+1 has energy >= that at rung q,
+// they trade rungs. If the top rung took no part in a trade for `timeout`
+// consecutive periods, top and bottom trade and the count restarts.
+__global__ void pt_exchange_kernel(int nsets, int ladder, const int64_t *energy, int32_t *rung,
+                                   int32_t *since_top, int timeout) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nsets) return;
+    int at[64];
+    const int base = g * ladder;
+    for (int k = 0; k < ladder; ++k) at[rung[base + k]] = k;
+    bool top = false;
+    for (int q = 0; q + 1 < ladder; ++q) {
+        const int lo = at[q], hi = at[q + 1];
+        if (energy[base + hi] >= energy[base + lo]) {
+            at[q] = hi;
+            at[q + 1] = lo;
+            if (q + 1 == ladder - 1) top = true;
+        }
+    }
+    int c = top ? 0 : since_top[g] + 1;
+    if (timeout > 0 && c >= timeout) {
+        const int t = at[ladder - 1];
+        at[ladder - 1] = at[0];
+        at[0] = t;
+        c = 0;
+    }
+    since_top[g] = c;
+    for (int q = 0; q < ladder; ++q) rung[base + at[q]] = q;
+}
+
+// Smallest best energy over replicas, ties to the lowest index; copies the
+// winner's permutation. One block.
+__global__ void finalize_kernel(int replicas, int n, const int64_t *best_energy,
+                                const int32_t *best_perm, int32_t *out_perm, int64_t *out_cost,
+                                const int32_t *status_in, int32_t *status_out) {
+    __shared__ long long sval[32];
+    __shared__ int sidx[32];
+    __shared__ int winner;
+    long long v = 0x7FFFFFFFFFFFFFFFll;
+    int idx = 0x7FFFFFFF;
+    for (int r = threadIdx.x; r < replicas; r += blockDim.x) {
+        const long long e = best_energy[r];
+        if (e < v || (e == v && r < idx)) {
+            v = e;
+            idx = r;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const long long ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, idx, o);
+        if (ov < v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sval[warp] = v;
+        sidx[warp] = idx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) / 32;
+        long long bv = sval[0];
+        int bi = sidx[0];
+        for (int w = 1; w < nw; ++w)
+            if (sval[w] < bv || (sval[w] == bv && sidx[w] < bi)) {
+                bv = sval[w];
+                bi = sidx[w];
+            }
+        winner = bi;
+        *out_cost = bv;
+        if (status_out) *status_out = *status_in;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < n; m += blockDim.x) out_perm[m] = best_perm[(size_t)winner * n + m];
+}
+
+int validate_opts(const pdit_qap *h, const pdit_opts *o) {
+    if (!h || !o) return PDIT_EINVAL;
+    if (o->struct_size != sizeof(pdit_opts)) return PDIT_EINVAL;
+    if (o->replicas < 1 || o->sweeps < 0) return PDIT_EINVAL;
+    const int se = o->sweep_end < 0 ? o->sweeps : o->sweep_end;
+    if (o->sweep_begin < 0 || se < o->sweep_begin || se > o->sweeps) return PDIT_EINVAL;
+    if ((uint64_t)o->sweeps >= 0xFFFFFFFFull) return PDIT_EINVAL;
+    if (!o->best_perm || !o->best_cost) return PDIT_EINVAL;
+    if (se > o->sweep_begin && !o->beta) return PDIT_EINVAL;
+    if (o->mode != PDIT_MODE_ANNEAL && o->mode != PDIT_MODE_PT) return PDIT_EINVAL;
+    if (o->mode == PDIT_MODE_PT) {
+        if (o->ladder_len < 2 || o->ladder_len > 64 || o->replicas % o->ladder_len) return PDIT_EINVAL;
+        if (o->exchange_period < 1 || o->timeout_periods < 0) return PDIT_EINVAL;
+        if (o->replica_base % (uint32_t)o->ladder_len) return PDIT_EINVAL;
+    }
+    if (!(o->flags & PDIT_FLAG_RESUME) && o->sweep_begin != 0) return PDIT_EINVAL;
+    return PDIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pdit_strerror(int code) {
+    switch (code) {
+    case PDIT_OK: return "success";
+    case PDIT_EINVAL: return "invalid argument";
+    case PDIT_ERANGE: return "instance values too large for exact int32 influence arithmetic";
+    case PDIT_ENOMEM: return "out of memory or workspace too small";
+    case PDIT_ECUDA: return "CUDA runtime error";
+    case PDIT_EDEVICE: return "device consistency audit failed";
+    case PDIT_ENOTSUP: return "not supported by this build";
+    default: return "unknown error";
+    }
+}
+
+const char *pdit_last_error(void) { return g_last_error.c_str(); }
+
+void pdit_opts_init(pdit_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(pdit_opts);
+    o->sweep_end = -1;
+    o->mode = PDIT_MODE_ANNEAL;
+    o->exchange_period = 4;
+    o->timeout_periods = 100;
+}
+
+int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
+    if (!out) return PDIT_EINVAL;
+    *out = nullptr;
+    if (n < 2 || n > PDIT_N_MAX || !D || !F) return PDIT_EINVAL;
+    int64_t maxd = 0, maxf = 0;
+    bool zd = true;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const int32_t d = D[(size_t)i * n + j], f = F[(size_t)i * n + j];
+            if (d != D[(size_t)j * n + i] || f != F[(size_t)j * n + i]) return PDIT_EINVAL;
+            maxd = std::max<int64_t>(maxd, std::llabs((long long)d));
+            maxf = std::max<int64_t>(maxf, std::llabs((long long)f));
+            if (i == j && (d != 0 || f != 0)) zd = false;
+        }
+    // |I| <= n maxD maxF, |dE| <= 8 n maxD maxF + 16 maxD maxF, and shifted
+    // energies span twice that: all of it stays inside int32.
+    if ((int64_t)16 * (n + 2) * maxd * maxf >= ((int64_t)1 << 31)) return PDIT_ERANGE;
+    pdit_qap *h = new (std::nothrow) pdit_qap();
+    if (!h) return PDIT_ENOMEM;
+    h->n = n;
+    h->zero_diag = zd ? 1 : 0;
+    const int64_t mx = std::max(maxd, maxf);
+    h->dt_bytes = mx <= 127 ? 1 : (mx <= 32767 ? 2 : 4);
+    h->hD.assign(D, D + (size_t)n * n);
+    h->hF.assign(F, F + (size_t)n * n);
+    cudaError_t e = cudaGetDevice(&h->device);
+    int v = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    h->smem_optin = (size_t)v;
+    const size_t bytes = sizeof(int32_t) * (size_t)n * n;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->dD, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->dF, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(h->dD, D, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->dF, F, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        const int rc = (e == cudaErrorMemoryAllocation) ? PDIT_ENOMEM : cuda_fail(e, "qap_create");
+        qap_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return PDIT_OK;
+}
+
+void qap_destroy(pdit_qap *h) {
+    if (!h) return;
+    int cur = 0;
+    const bool have = cudaGetDevice(&cur) == cudaSuccess;
+    if (have && cur != h->device) cudaSetDevice(h->device);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    cudaFree(h->dD);
+    cudaFree(h->dF);
+    cudaFree(h->ws);
+    cudaFree(h->dbeta);
+    cudaFree(h->dperm);
+    cudaFree(h->dcost);
+    cudaFree(h->dstatus);
+    if (have && cur != h->device) cudaSetDevice(cur);
+    delete h;
+}
+
+int qap_n(const pdit_qap *h) { return h ? h->n : PDIT_EINVAL; }
+
+size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o) {
+    if (!h || !o || o->replicas < 1) return 0;
+    Plan p;
+    if (make_plan(h, o->replicas, &p) != PDIT_OK) return 0;
+    return carve(h, o, p, nullptr).bytes;
+}
+
+int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
+    int rc = validate_opts(h, o);
+    if (rc) return rc;
+    Plan plan;
+    rc = make_plan(h, o->replicas, &plan);
+    if (rc) return rc;
+    const size_t need = carve(h, o, plan, nullptr).bytes;
+    char *base = (char *)o->workspace;
+    if (base) {
+        if (o->workspace_bytes < need) return PDIT_ENOMEM;
+    } else {
+        if (h->ws_bytes < need) {
+            if (o->flags & PDIT_FLAG_RESUME) return PDIT_EINVAL;  // no state to resume from
+            cudaFree(h->ws);
+            h->ws = nullptr;
+            h->ws_bytes = 0;
+            cudaError_t e = cudaMalloc(&h->ws, need);
+            if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PDIT_ENOMEM : cuda_fail(e, "workspace");
+            h->ws_bytes = need;
+        }
+        base = (char *)h->ws;
+    }
+    const Workspace w = carve(h, o, plan, base);
+    cudaStream_t st = (cudaStream_t)o->stream;
+    const bool resume = (o->flags & PDIT_FLAG_RESUME) != 0;
+    const int sb = o->sweep_begin;
+    const int se = o->sweep_end < 0 ? o->sweeps : o->sweep_end;
+    const int R = o->replicas;
+    const bool pt = o->mode == PDIT_MODE_PT;
+
+    if (!resume) {
+        PDIT_CK(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+        if (pt) {
+            init_pt_kernel<<<(R + 255) / 256, 256, 0, st>>>(R, o->ladder_len, w.rung, w.since_top,
+                                                            o->replica_base);
+            PDIT_CK(cudaGetLastError());
+        }
+    }
+
+    pdit::SweepArgs a{};
+    a.D = h->dD;
+    a.F = h->dF;
+    a.n = h->n;
+    a.stride = plan.stride;
+    a.zero_diag = h->zero_diag;
+    a.replicas = R;
+    a.key0 = (uint32_t)o->seed;
+    a.key1 = (uint32_t)(o->seed >> 32);
+    a.inst = o->instance_id;
+    a.rep_base = o->replica_base;
+    a.mode = pt ? 1 : 0;
+    a.beta = o->beta;
+    a.perm = w.perm;
+    a.best_perm = w.best_perm;
+    a.energy = w.energy;
+    a.best_energy = w.best_energy;
+    a.best_sweep = w.best_sweep;
+    a.accepted = w.accepted;
+    a.rung = w.rung;
+    a.tables = w.tables;
+    a.queue = w.queue;
+    a.status = w.status;
+    a.df_bytes = plan.df_bytes;
+    a.warp_bytes = plan.warp_bytes;
+
+    // Segments: the whole range in anneal mode; exchange periods in PT mode.
+    bool first = true;
+    int s = sb;
+    do {
+        int next = se;
+        if (pt) next = std::min(se, (s / o->exchange_period + 1) * o->exchange_period);
+        a.sweep_begin = s;
+        a.sweep_end = next;
+        a.fresh = (!resume && first) ? 1 : 0;
+        // Tables persist across segments in PT mode; the global-table path
+        // always works in place.
+        a.table_in = (pt && !(first && !resume)) || (!plan.tsmem && !a.fresh && pt) ? 1 : 0;
+        a.table_out = pt ? 1 : 0;
+        a.dump = (next == se) ? o->tables : nullptr;
+        if (!(first && resume && s == se)) {
+            PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
+            const int e = sweep_launch(h->dt_bytes, plan.maxk, plan.tsmem, a, plan.grid, plan.threads,
+                                       plan.smem, st);
+            if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
+        }
+        if (pt && next < se + 1 && next % o->exchange_period == 0 && next > s) {
+            const int nsets = R / o->ladder_len;
+            pt_exchange_kernel<<<(nsets + 127) / 128, 128, 0, st>>>(nsets, o->ladder_len, w.energy, w.rung,
+                                                                   w.since_top, o->timeout_periods);
+            PDIT_CK(cudaGetLastError());
+        }
+        first = false;
+        s = next;
+    } while (s < se);
+
+    finalize_kernel<<<1, 1024, 0, st>>>(R, h->n, w.best_energy, w.best_perm, o->best_perm, o->best_cost,
+                                        w.status, o->status);
+    PDIT_CK(cudaGetLastError());
+    const size_t n = (size_t)h->n;
+    if (o->replica_best_cost)
+        PDIT_CK(cudaMemcpyAsync(o->replica_best_cost, w.best_energy, 8 * R, cudaMemcpyDeviceToDevice, st));
+    if (o->replica_best_perm)
+        PDIT_CK(cudaMemcpyAsync(o->replica_best_perm, w.best_perm, 4 * R * n, cudaMemcpyDeviceToDevice, st));
+    if (o->replica_best_sweep)
+        PDIT_CK(cudaMemcpyAsync(o->replica_best_sweep, w.best_sweep, 4 * R, cudaMemcpyDeviceToDevice, st));
+    if (o->replica_final_perm)
+        PDIT_CK(cudaMemcpyAsync(o->replica_final_perm, w.perm, 4 * R * n, cudaMemcpyDeviceToDevice, st));
+    if (o->replica_final_cost)
+        PDIT_CK(cudaMemcpyAsync(o->replica_final_cost, w.energy, 8 * R, cudaMemcpyDeviceToDevice, st));
+    if (o->replica_accepted)
+        PDIT_CK(cudaMemcpyAsync(o->replica_accepted, w.accepted, 8 * R, cudaMemcpyDeviceToDevice, st));
+    if (o->replica_rung && pt)
+        PDIT_CK(cudaMemcpyAsync(o->replica_rung, w.rung, 4 * R, cudaMemcpyDeviceToDevice, st));
+    return PDIT_OK;
+}
+
+int pdit_anneal(pdit_qap *h, int replicas, const float *beta_schedule, int sweeps, uint64_t seed,
+                int32_t *best_perm, int64_t *best_cost) {
+    if (!h || replicas < 1 || sweeps < 0 || !best_perm || !best_cost) return PDIT_EINVAL;
+    if (sweeps > 0 && !beta_schedule) return PDIT_EINVAL;
+    for (int s = 0; s < sweeps; ++s)
+        if (!(beta_schedule[s] >= 0.0f) || !std::isfinite(beta_schedule[s])) return PDIT_EINVAL;
+    if (!h->stream) PDIT_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    if (!h->dperm) PDIT_CK(cudaMalloc((void **)&h->dperm, sizeof(int32_t) * h->n));
+    if (!h->dcost) PDIT_CK(cudaMalloc((void **)&h->dcost, sizeof(int64_t)));
+    if (!h->dstatus) PDIT_CK(cudaMalloc((void **)&h->dstatus, sizeof(int32_t)));
+    const size_t nb = (size_t)std::max(sweeps, 1);
+    if (h->dbeta_cap < nb) {
+        cudaFree(h->dbeta);
+        h->dbeta = nullptr;
+        h->dbeta_cap = 0;
+        PDIT_CK(cudaMalloc((void **)&h->dbeta, sizeof(float) * nb));
+        h->dbeta_cap = nb;
+    }
+    if (sweeps > 0)
+        PDIT_CK(cudaMemcpyAsync(h->dbeta, beta_schedule, sizeof(float) * sweeps, cudaMemcpyHostToDevice,
+                                h->stream));
+    pdit_opts o;
+    pdit_opts_init(&o);
+    o.replicas = replicas;
+    o.sweeps = sweeps;
+    o.seed = seed;
+    o.beta = h->dbeta;
+    o.stream = h->stream;
+    o.best_perm = h->dperm;
+    o.best_cost = h->dcost;
+    o.status = h->dstatus;
+    int rc = pdit_anneal_ex(h, &o);
+    if (rc) return rc;
+    int32_t status = 0;
+    PDIT_CK(cudaMemcpyAsync(best_perm, h->dperm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream));
+    PDIT_CK(cudaMemcpyAsync(best_cost, h->dcost, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    PDIT_CK(cudaMemcpyAsync(&status, h->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    PDIT_CK(cudaStreamSynchronize(h->stream));
+    return status ? PDIT_EDEVICE : PDIT_OK;
+}
+
+int pdit_beta_max(const pdit_qap *h, double *beta_max) {
+    if (!h || !beta_max) return PDIT_EINVAL;
+    const int n = h->n;
+    const int32_t *D = h->hD.data(), *F = h->hF.data();
+    // Identity permutation: I[m][c] = sum_j D[m][j] F[c][j].
+    std::vector<int64_t> I((size_t)n * n, 0);
+    for (int m = 0; m < n; ++m)
+        for (int j = 0; j < n; ++j) {
+            const int64_t d = D[(size_t)m * n + j];
+            if (!d) continue;
+            for (int c = 0; c < n; ++c) I[(size_t)m * n + c] += d * F[(size_t)c * n + j];
+        }
+    double sum = 0.0;
+    long long cnt = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            // Eq. 3 with a = i, b = j (identity permutation), symmetric D and F.
+            const int64_t t = I[(size_t)i * n + j] - I[(size_t)i * n + i] + I[(size_t)j * n + i] -
+                              I[(size_t)j * n + j];
+            const int64_t dd = (int64_t)D[(size_t)i * n + i] + D[(size_t)j * n + j] - 2 * (int64_t)D[(size_t)i * n + j];
+            const int64_t ff = (int64_t)F[(size_t)i * n + i] + F[(size_t)j * n + j] - 2 * (int64_t)F[(size_t)i * n + j];
+            const int64_t de = 2 * t + dd * ff;
+            if (de > 0) {
+                sum += (double)de;
+                ++cnt;
+            }
+        }
+    *beta_max = cnt ? 10.0 / (sum / (double)cnt) : 1.0;
+    return PDIT_OK;
+}
+
+int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out) {
+    if (sweeps < 0 || (sweeps > 0 && !out) || (kind != 0 && kind != 1)) return PDIT_EINVAL;
+    if (!(beta_max >= 0.0) || !std::isfinite(beta_max)) return PDIT_EINVAL;
+    for (int s = 0; s < sweeps; ++s) {
+        const double f = sweeps > 1 ? (double)s / (double)(sweeps - 1) : 1.0;
+        const double b = kind == 0 ? beta_max * f : (beta_max / 1000.0) * std::pow(1000.0, f);
+        out[s] = (float)b;
+    }
+    return PDIT_OK;
+}
+
+}  // extern "C"

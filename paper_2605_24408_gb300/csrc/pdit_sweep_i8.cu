@@ -1,0 +1,6 @@
+// Sweep kernels with D and F staged as int8_t (see pdit_sweep.cuh).
+#include "pdit_sweep.cuh"
+
+namespace pdit {
+PDIT_INSTANTIATE_SWEEP(int8_t)
+}  // namespace pdit

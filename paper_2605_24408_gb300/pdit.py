@@ -1,0 +1,276 @@
+"""Python binding of libpdit (include/pdit.h): argument marshalling only.
+
+Every step of the annealed p-dit sweep runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams for the device-buffer entry
+point. If libpdit.so has not been built this module raises on import of the
+library; there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpdit.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "pdit.h")
+
+PDIT_OK = 0
+PDIT_EINVAL = -1
+PDIT_ERANGE = -2
+PDIT_ENOMEM = -3
+PDIT_ECUDA = -4
+PDIT_EDEVICE = -5
+PDIT_ENOTSUP = -6
+PDIT_N_MAX = 256
+PDIT_MODE_ANNEAL = 0
+PDIT_MODE_PT = 1
+PDIT_FLAG_RESUME = 1
+
+_lib = None
+
+
+class PditError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = "%s failed: %s (%d)" % (what, strerror(code), code)
+        if code == PDIT_ECUDA:
+            msg += ": " + last_error()
+        super().__init__(msg)
+        self.code = code
+
+
+class pdit_opts(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("replicas", ctypes.c_int),
+        ("sweeps", ctypes.c_int),
+        ("sweep_begin", ctypes.c_int),
+        ("sweep_end", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+        ("instance_id", ctypes.c_uint32),
+        ("replica_base", ctypes.c_uint32),
+        ("mode", ctypes.c_int),
+        ("beta", ctypes.c_void_p),
+        ("ladder_len", ctypes.c_int),
+        ("exchange_period", ctypes.c_int),
+        ("timeout_periods", ctypes.c_int),
+        ("flags", ctypes.c_uint32),
+        ("stream", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("best_perm", ctypes.c_void_p),
+        ("best_cost", ctypes.c_void_p),
+        ("replica_best_cost", ctypes.c_void_p),
+        ("replica_best_perm", ctypes.c_void_p),
+        ("replica_best_sweep", ctypes.c_void_p),
+        ("replica_final_perm", ctypes.c_void_p),
+        ("replica_final_cost", ctypes.c_void_p),
+        ("replica_accepted", ctypes.c_void_p),
+        ("replica_rung", ctypes.c_void_p),
+        ("tables", ctypes.c_void_p),
+        ("status", ctypes.c_void_p),
+    ]
+
+
+def lib():
+    """Load libpdit.so (built by paper_2605_24408_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libpdit.so is not built (run __graft_entry__.build()); "
+                           "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32p, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    L.qap_create.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(vp)]
+    L.qap_create.restype = ctypes.c_int
+    L.qap_destroy.argtypes = [vp]
+    L.qap_destroy.restype = None
+    L.qap_n.argtypes = [vp]
+    L.qap_n.restype = ctypes.c_int
+    L.pdit_anneal.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_uint64, vp, vp]
+    L.pdit_anneal.restype = ctypes.c_int
+    L.pdit_opts_init.argtypes = [ctypes.POINTER(pdit_opts)]
+    L.pdit_opts_init.restype = None
+    L.pdit_workspace_bytes.argtypes = [vp, ctypes.POINTER(pdit_opts)]
+    L.pdit_workspace_bytes.restype = ctypes.c_size_t
+    L.pdit_anneal_ex.argtypes = [vp, ctypes.POINTER(pdit_opts)]
+    L.pdit_anneal_ex.restype = ctypes.c_int
+    L.pdit_beta_max.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.pdit_beta_max.restype = ctypes.c_int
+    L.pdit_beta_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]
+    L.pdit_beta_schedule.restype = ctypes.c_int
+    L.pdit_strerror.argtypes = [ctypes.c_int]
+    L.pdit_strerror.restype = ctypes.c_char_p
+    L.pdit_last_error.argtypes = []
+    L.pdit_last_error.restype = ctypes.c_char_p
+    del i32p, i64p
+    _lib = L
+    return L
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/pdit.h."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)) -
+                  {"if", "sizeof", "for", "while", "return"})
+
+
+def strerror(code: int) -> str:
+    return lib().pdit_strerror(code).decode()
+
+
+def last_error() -> str:
+    return lib().pdit_last_error().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != PDIT_OK:
+        raise PditError(rc, what)
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# --- handle ------------------------------------------------------------------
+
+class Qap:
+    """An uploaded instance (qap_create / qap_destroy)."""
+
+    def __init__(self, D, F):
+        D = np.ascontiguousarray(D, dtype=np.int32)
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        if D.ndim != 2 or D.shape[0] != D.shape[1] or F.shape != D.shape:
+            raise ValueError("D and F must be square and of the same shape")
+        self.n = int(D.shape[0])
+        h = ctypes.c_void_p()
+        _check(lib().qap_create(self.n, _ptr(D), _ptr(F), ctypes.byref(h)), "qap_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qap_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def qap_create(D, F) -> Qap:
+    return Qap(D, F)
+
+
+def qap_destroy(q: Qap):
+    q.close()
+
+
+def pdit_anneal(q: Qap, replicas: int, beta_schedule, sweeps: int, seed: int):
+    """Host-buffer entry point. Returns (best permutation int32[n], best cost)."""
+    beta = np.ascontiguousarray(beta_schedule, dtype=np.float32)
+    if beta.size < sweeps:
+        raise ValueError("beta_schedule shorter than sweeps")
+    perm = np.zeros(q.n, dtype=np.int32)
+    cost = np.zeros(1, dtype=np.int64)
+    _check(lib().pdit_anneal(q.handle, replicas, _ptr(beta) if sweeps else None, sweeps,
+                             seed & 0xFFFFFFFFFFFFFFFF, _ptr(perm), _ptr(cost)), "pdit_anneal")
+    return perm, int(cost[0])
+
+
+def pdit_anneal_host_ptrs(q: Qap, replicas: int, beta_ptr: int, sweeps: int, seed: int,
+                          perm_ptr: int, cost_ptr: int) -> int:
+    """pdit_anneal on raw host pointers (for pinned buffers); returns the code."""
+    return lib().pdit_anneal(q.handle, replicas, ctypes.c_void_p(beta_ptr), sweeps,
+                             seed & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(perm_ptr),
+                             ctypes.c_void_p(cost_ptr))
+
+
+def pdit_beta_max(q: Qap) -> float:
+    out = ctypes.c_double()
+    _check(lib().pdit_beta_max(q.handle, ctypes.byref(out)), "pdit_beta_max")
+    return float(out.value)
+
+
+def pdit_beta_schedule(kind: str, sweeps: int, beta_max: float) -> np.ndarray:
+    out = np.zeros(max(sweeps, 1), dtype=np.float32)
+    _check(lib().pdit_beta_schedule({"linear": 0, "geometric": 1}[kind], sweeps, beta_max, _ptr(out)),
+           "pdit_beta_schedule")
+    return out[:sweeps]
+
+
+def opts(**kw) -> pdit_opts:
+    o = pdit_opts()
+    lib().pdit_opts_init(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def pdit_workspace_bytes(q: Qap, o: pdit_opts) -> int:
+    return int(lib().pdit_workspace_bytes(q.handle, ctypes.byref(o)))
+
+
+def pdit_anneal_ex(q: Qap, o: pdit_opts):
+    _check(lib().pdit_anneal_ex(q.handle, ctypes.byref(o)), "pdit_anneal_ex")
+
+
+# --- torch convenience (device buffers, current stream) ----------------------
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def anneal_device(q: Qap, replicas: int, beta, sweeps: int, seed: int, *, mode: int = PDIT_MODE_ANNEAL,
+                  ladder_len: int = 0, exchange_period: int = 4, timeout_periods: int = 100,
+                  instance_id: int = 0, replica_base: int = 0, sweep_begin: int = 0,
+                  sweep_end: int = -1, resume: bool = False, workspace=None, per_replica: bool = False,
+                  tables: bool = False, stream=None):
+    """pdit_anneal_ex on torch device tensors. `beta` is a CUDA float32 tensor.
+    Returns a dict of device tensors (asynchronous on the current stream)."""
+    import torch
+
+    dev = beta.device
+    n, R = q.n, replicas
+    out = {"best_perm": torch.empty(n, dtype=torch.int32, device=dev),
+           "best_cost": torch.empty(1, dtype=torch.int64, device=dev),
+           "status": torch.zeros(1, dtype=torch.int32, device=dev)}
+    if per_replica:
+        out.update(replica_best_cost=torch.empty(R, dtype=torch.int64, device=dev),
+                   replica_best_perm=torch.empty(R, n, dtype=torch.int32, device=dev),
+                   replica_best_sweep=torch.empty(R, dtype=torch.int32, device=dev),
+                   replica_final_perm=torch.empty(R, n, dtype=torch.int32, device=dev),
+                   replica_final_cost=torch.empty(R, dtype=torch.int64, device=dev),
+                   replica_accepted=torch.empty(R, dtype=torch.int64, device=dev))
+        if mode == PDIT_MODE_PT:
+            out["replica_rung"] = torch.empty(R, dtype=torch.int32, device=dev)
+    if tables:
+        out["tables"] = torch.empty(R, n, n, dtype=torch.int32, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    o = opts(replicas=R, sweeps=sweeps, seed=seed & 0xFFFFFFFFFFFFFFFF, instance_id=instance_id,
+             replica_base=replica_base, mode=mode, beta=beta.data_ptr(), ladder_len=ladder_len,
+             exchange_period=exchange_period, timeout_periods=timeout_periods,
+             sweep_begin=sweep_begin, sweep_end=sweep_end,
+             flags=PDIT_FLAG_RESUME if resume else 0, stream=st.cuda_stream)
+    if workspace is None:
+        need = pdit_workspace_bytes(q, o)
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    o.workspace = workspace.data_ptr()
+    o.workspace_bytes = workspace.numel()
+    for k, t in out.items():
+        setattr(o, k, t.data_ptr())
+    pdit_anneal_ex(q, o)
+    out["workspace"] = workspace
+    return out
