@@ -195,6 +195,10 @@ def main():
     ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--wpr", type=int, default=0,
+                    help="warps per replica (0: the library's choice)")
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="override the workload's sweep count (smaller cases for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -221,9 +225,14 @@ def main():
         dist.barrier()
 
     inst, replicas, sweeps, kind = WORKLOADS[args.workload]
+    if args.sweeps > 0:
+        sweeps = args.sweeps
     D, F = G.named(inst)
     n = D.shape[0]
     q = P.Qap(D, F)
+    if args.wpr:
+        P.pdit_set_warps_per_replica(q, args.wpr)
+    shape = P.pdit_launch_shape(q, replicas)
     beta = P.pdit_beta_schedule(kind, sweeps, P.pdit_beta_max(q))
     dev = torch.device("cuda", local)
     dbeta = torch.from_numpy(beta).to(dev)
@@ -303,8 +312,9 @@ def main():
             raise SystemExit("pdit_anneal failed: %s" % P.strerror(rc))
         if k > 0:  # the first call allocates the handle's buffers
             e2e_t.append(t1 - t0)
-    e2e_val = world * upd_rank * len(e2e_t) / sum(e2e_t)
-    assert int(hcost[0]) == int(outs["best_cost"].item()) or dist is not None
+    e2e_val = world * upd_rank * len(e2e_t) / sum(e2e_t) if e2e_t else None
+    if e2e_t and dist is None and int(hcost[0]) != int(outs["best_cost"].item()):
+        raise SystemExit("host-buffer and device-buffer results differ")
 
     # roofline of the sweep kernel: shared-memory bound
     props = torch.cuda.get_device_properties(dev)
@@ -333,7 +343,7 @@ def main():
                    "global_batch": replicas * world, "seq_len": n,
                    "parallelism": "replicas sharded over %d GPU(s)" % world,
                    "l2": "flushed between timed steps (512 MiB write)",
-                   "accept_fraction": accept_frac, "best_cost": best_cost},
+                   "accept_fraction": accept_frac, "best_cost": best_cost, "launch": shape},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 4 * sweeps,
                 "d2h_bytes_per_step": 4 * n + 8 + 4},
         "gpu_launches": 2 * args.steps,
@@ -341,7 +351,9 @@ def main():
                    "reasons": clk.get("reasons"), "samples": clk.get("samples")},
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if peak else None, "traffic": traffic,
-                     "kernel": "sweep_kernel<int8,4,smem>",
+                     "kernel": "sweep_kernel<int8,%d,%d,%s>" % (shape["candidates_per_thread"],
+                                                                shape["warps_per_replica"],
+                                                                "smem" if shape["tables_in_smem"] else "global"),
                      "bytes_per_update": bpu,
                      "peak_source": "derived: %d SMs x %d B/clk x median SM clock under load (%s MHz)"
                                     % (props.multi_processor_count, SMEM_BYTES_PER_CLK, sm_mhz)},

@@ -82,6 +82,25 @@ void qap_destroy(pdit_qap *h);
 int qap_n(const pdit_qap *h);
 
 /*
+ * pdit_set_warps_per_replica -- thread mapping of later calls on this
+ * handle: each replica is updated by `wpr` warps (1, 2, 4 or 8, at most
+ * ceil(n/32) rounded up to a power of two); 0 restores the built-in choice.
+ * Results do not depend on it (the paper parallelises each update across
+ * threads, GPU Implementations section; the split is a performance knob).
+ * Errors: PDIT_EINVAL.
+ */
+int pdit_set_warps_per_replica(pdit_qap *h, int wpr);
+
+/*
+ * pdit_launch_shape -- the sweep-kernel launch a call with `replicas` chains
+ * would use: shape[0] warps per replica, [1] candidates per thread, [2]
+ * replicas per CTA, [3] CTAs, [4] 1 if the influence tables live in shared
+ * memory (0: global memory), [5] dynamic shared memory bytes per CTA.
+ * `shape` is a host array of 6 ints. Errors: PDIT_EINVAL, PDIT_ENOTSUP.
+ */
+int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape);
+
+/*
  * pdit_anneal -- synchronous annealed p-dit sweep on HOST buffers.
  *   replicas      : >= 1 independent chains (replica ids 0..replicas-1).
  *   beta_schedule : host, `sweeps` floats, beta of sweep s (finite, >= 0).

@@ -30,6 +30,7 @@ struct pdit_qap {
     int64_t *dcost = nullptr;
     int32_t *dstatus = nullptr;
     cudaStream_t stream = nullptr;
+    int force_wpr = 0;      // warps per replica; 0 = chosen per launch
 };
 
 namespace {
@@ -58,67 +59,77 @@ int table_stride(int n) {
     return s;
 }
 
-int maxk_for(int n) {
-    int k = (n + 31) / 32;
-    int p = 1;
-    while (p < k) p <<= 1;
-    return p;
+// Candidates covered by one group: 32 * WPR * MAXK, a power of two >= n.
+int cover_for(int n) {
+    int c = 32;
+    while (c < n) c <<= 1;
+    return c;
 }
-
-int warp_cap(int maxk) { return maxk == 1 ? 32 : (maxk == 2 ? 16 : (maxk == 4 ? 12 : 4)); }
 
 struct Plan {
-    int maxk = 1;
+    int maxk = 1, wpr = 1;
     bool tsmem = true;
     int stride = 0;
-    size_t df_bytes = 0, warp_bytes = 0, smem = 0;
-    int warps = 1, threads = 32, grid = 1;
+    size_t df_bytes = 0, group_bytes = 0, smem = 0;
+    int groups = 1, threads = 32, grid = 1;
 };
 
-int sweep_blocks(int dt, int maxk, bool tsmem, int threads, size_t smem, int *blocks) {
-    if (dt == 1) return pdit::sweep_blocks_per_sm<int8_t>(maxk, tsmem, threads, smem, blocks);
-    if (dt == 2) return pdit::sweep_blocks_per_sm<int16_t>(maxk, tsmem, threads, smem, blocks);
-    return pdit::sweep_blocks_per_sm<int32_t>(maxk, tsmem, threads, smem, blocks);
+
+int sweep_blocks(int dt, const Plan &p, int *blocks) {
+    if (dt == 1) return pdit::sweep_blocks_per_sm<int8_t>(p.maxk, p.wpr, p.tsmem, p.threads, p.smem, blocks);
+    if (dt == 2) return pdit::sweep_blocks_per_sm<int16_t>(p.maxk, p.wpr, p.tsmem, p.threads, p.smem, blocks);
+    return pdit::sweep_blocks_per_sm<int32_t>(p.maxk, p.wpr, p.tsmem, p.threads, p.smem, blocks);
 }
 
-int sweep_launch(int dt, int maxk, bool tsmem, const pdit::SweepArgs &a, int grid, int threads,
-                 size_t smem, cudaStream_t st) {
-    if (dt == 1) return pdit::sweep_launch<int8_t>(maxk, tsmem, a, grid, threads, smem, st);
-    if (dt == 2) return pdit::sweep_launch<int16_t>(maxk, tsmem, a, grid, threads, smem, st);
-    return pdit::sweep_launch<int32_t>(maxk, tsmem, a, grid, threads, smem, st);
+int sweep_launch(int dt, const Plan &p, const pdit::SweepArgs &a, cudaStream_t st) {
+    if (dt == 1) return pdit::sweep_launch<int8_t>(p.maxk, p.wpr, p.tsmem, a, p.grid, p.threads, p.smem, st);
+    if (dt == 2) return pdit::sweep_launch<int16_t>(p.maxk, p.wpr, p.tsmem, a, p.grid, p.threads, p.smem, st);
+    return pdit::sweep_launch<int32_t>(p.maxk, p.wpr, p.tsmem, a, p.grid, p.threads, p.smem, st);
 }
 
-// Launch shape for `replicas` chains of an n-location instance.
-int make_plan(const pdit_qap *h, int replicas, Plan *p) {
-    const int n = h->n;
-    p->maxk = maxk_for(n);
-    p->stride = table_stride(n);
+// Shared-memory slice of one replica group for a given shape.
+size_t group_bytes_for(int n, int stride, int cover, bool tsmem) {
     const size_t npad = (size_t)((n + 3) & ~3);
-    const size_t svn = std::max((size_t)p->stride, (size_t)(32 * p->maxk));
+    const size_t svn = std::max((size_t)stride, (size_t)cover);
+    const size_t vec = 4 * (2 * npad + svn);
+    const size_t table = tsmem ? (size_t)4 * n * stride : 0;
+    return align_up(pdit::kScratchBytes + table + vec, 16);
+}
+
+// Launch shape for `replicas` chains of an n-location instance. `wpr` = warps
+// per replica (0: choose).
+int make_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
+    const int n = h->n;
+    const int cover = cover_for(n);
+    p->stride = table_stride(n);
     p->df_bytes = align_up((size_t)2 * n * n * h->dt_bytes, 16);
-    const size_t vec_bytes = 4 * (2 * npad + svn);
-    const size_t table_bytes = (size_t)4 * n * p->stride;
     const size_t budget = h->smem_optin;
-    size_t wb = align_up(table_bytes + vec_bytes, 16);
-    p->tsmem = p->df_bytes + wb <= budget;
-    if (!p->tsmem) {
-        if (p->maxk < 4) return PDIT_ENOTSUP;
-        wb = align_up(vec_bytes, 16);
-        if (p->df_bytes + wb > budget) return PDIT_ENOTSUP;
+    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true) <= budget;
+    if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;
+    p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem);
+    if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
+    const int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
+    if (wpr <= 0) {
+        // Aim for about 16 resident warps per SM to hide the latency of each
+        // replica's sequential update chain.
+        wpr = 1;
+        while (wpr < cover / 32 && std::min(fit, 32 / wpr) * wpr < 16) wpr <<= 1;
     }
-    p->warp_bytes = wb;
-    int w = (int)((budget - p->df_bytes) / wb);
-    w = std::min(w, warp_cap(p->maxk));
+    if (wpr < 1 || wpr > cover / 32 || (wpr & (wpr - 1))) return PDIT_EINVAL;
+    p->wpr = wpr;
+    p->maxk = cover / (32 * wpr);
+    int g = std::min(fit, pdit::sweep_bound(p->maxk, wpr) / (32 * wpr));
+    if (wpr > 1) g = std::min(g, 15);  // named barriers 1..15
     const int per_sm = (replicas + h->num_sms - 1) / h->num_sms;
-    w = std::max(1, std::min(w, per_sm));
-    p->warps = w;
-    p->threads = 32 * w;
-    p->smem = p->df_bytes + (size_t)w * wb;
+    g = std::max(1, std::min(g, per_sm));
+    p->groups = g;
+    p->threads = 32 * wpr * g;
+    p->smem = p->df_bytes + (size_t)g * p->group_bytes;
     int bps = 0;
-    int e = sweep_blocks(h->dt_bytes, p->maxk, p->tsmem, p->threads, p->smem, &bps);
+    int e = sweep_blocks(h->dt_bytes, *p, &bps);
     if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
     if (bps < 1) bps = 1;
-    const int need = (replicas + w - 1) / w;
+    const int need = (replicas + g - 1) / g;
     p->grid = std::max(1, std::min(need, h->num_sms * bps));
     return PDIT_OK;
 }
@@ -356,10 +367,31 @@ void qap_destroy(pdit_qap *h) {
 
 int qap_n(const pdit_qap *h) { return h ? h->n : PDIT_EINVAL; }
 
+int pdit_set_warps_per_replica(pdit_qap *h, int wpr) {
+    if (!h || wpr < 0 || wpr > 8 || (wpr & (wpr - 1))) return PDIT_EINVAL;
+    if (wpr > cover_for(h->n) / 32) return PDIT_EINVAL;
+    h->force_wpr = wpr;
+    return PDIT_OK;
+}
+
+int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape) {
+    if (!h || replicas < 1 || !shape) return PDIT_EINVAL;
+    Plan p;
+    const int rc = make_plan(h, replicas, h->force_wpr, &p);
+    if (rc) return rc;
+    shape[0] = p.wpr;
+    shape[1] = p.maxk;
+    shape[2] = p.groups;
+    shape[3] = p.grid;
+    shape[4] = p.tsmem ? 1 : 0;
+    shape[5] = (int)p.smem;
+    return PDIT_OK;
+}
+
 size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o) {
     if (!h || !o || o->replicas < 1) return 0;
     Plan p;
-    if (make_plan(h, o->replicas, &p) != PDIT_OK) return 0;
+    if (make_plan(h, o->replicas, h->force_wpr, &p) != PDIT_OK) return 0;
     return carve(h, o, p, nullptr).bytes;
 }
 
@@ -367,7 +399,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     int rc = validate_opts(h, o);
     if (rc) return rc;
     Plan plan;
-    rc = make_plan(h, o->replicas, &plan);
+    rc = make_plan(h, o->replicas, h->force_wpr, &plan);
     if (rc) return rc;
     const size_t need = carve(h, o, plan, nullptr).bytes;
     char *base = (char *)o->workspace;
@@ -426,7 +458,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.queue = w.queue;
     a.status = w.status;
     a.df_bytes = plan.df_bytes;
-    a.warp_bytes = plan.warp_bytes;
+    a.group_bytes = plan.group_bytes;
 
     // Segments: the whole range in anneal mode; exchange periods in PT mode.
     bool first = true;
@@ -444,8 +476,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.dump = (next == se) ? o->tables : nullptr;
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
-            const int e = sweep_launch(h->dt_bytes, plan.maxk, plan.tsmem, a, plan.grid, plan.threads,
-                                       plan.smem, st);
+            const int e = sweep_launch(h->dt_bytes, plan, a, st);
             if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
         }
         if (pt && next < se + 1 && next % o->exchange_period == 0 && next > s) {

@@ -1,20 +1,21 @@
 // Annealed p-dit sweep kernels for the symmetric QAP on sm_103a.
 //
-// One warp owns one replica at a time. A CTA stages the instance's D and F
-// once in shared memory (int8/int16/int32, whichever holds every value), and
-// each of its warps keeps its replica's influence table, permutation and
-// scratch vectors in its own slice of shared memory (or, when the table does
-// not fit, the table in global memory). Warps pull replicas from a global
-// atomic counter until none are left.
+// A replica is owned by a group of G = 32 * WPR threads (WPR warps, 1..8).
+// A CTA stages the instance's D and F once in shared memory (int8/int16/int32,
+// whichever holds every value), and each group keeps its replica's influence
+// table, permutation and scratch vectors in its own slice of shared memory
+// (or, when the table does not fit, the table in global memory). Groups pull
+// replicas from a global atomic counter until none are left.
 //
 // Per p-dit update (Eq. 5 over the N outcomes of location i):
-//   gather   lane j-interleaved: dE_j from Eq. 3 with the influence table,
-//            dE_i = 0 (stay)
-//   sample   warp min of dE, binary32 weights (the same arithmetic the CPU
-//            oracle states), lane-contiguous 64-bit prefix sums, one 64-bit
-//            Philox draw scaled by the total, first prefix above it
+//   gather   candidate j on thread j mod G: dE_j from Eq. 3 with the
+//            influence table, dE_i = 0 (stay)
+//   sample   group min of dE, binary32 weights (the arithmetic the CPU oracle
+//            states), thread-contiguous 64-bit prefix sums, one 64-bit Philox
+//            draw scaled by the total, first prefix above it
 //   apply    if a swap j* was drawn: I[m][c] += (D[i][m]-D[j*][m]) (F[b][c]-F[a][c])
-//            as int4 read-modify-writes, then p, the p-diagonal h and E
+//            as int4 read-modify-writes on each thread's rows, then p, the
+//            p-diagonal h and E
 //   best     first occurrence of a new minimum of E (strict <)
 // Sweeps visit locations 0..N-1 in order. Every integer is exact; the only
 // floating point is the weight computation, made of single correctly rounded
@@ -60,8 +61,18 @@ struct SweepArgs {
     int *status;           // audit bits
     // launch shape
     size_t df_bytes;       // bytes of staged D and F (16-byte multiple)
-    size_t warp_bytes;     // bytes of one warp's slice
+    size_t group_bytes;    // bytes of one group's slice
 };
+
+// Per-group scratch for cross-warp reductions and broadcasts.
+struct GroupScratch {
+    unsigned long long wtot[8];
+    int wmin[8];
+    int sel_j, sel_d;
+    int item;
+    int pad;
+};
+constexpr size_t kScratchBytes = sizeof(GroupScratch);  // 112
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10, from its published definition (Salmon, Moraes, Dror and
@@ -94,17 +105,22 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
 //   x = (float)(dE - dE_min) * beta
 //   w = 0 if x > 40, else trunc(e^-x * 2^53) as a uint64
 // e^-x: Cody-Waite reduction x = k ln2 + r (k nearest to x log2 e, ln 2 as a
-// 15-bit head plus its binary32 tail), Taylor polynomial of degree 7 for
-// e^-r in Horner form with fused multiply-adds, exact scaling by 2^-k.
+// 15-bit head plus its binary32 tail), Taylor polynomial q(r) of degree 7 for
+// e^-r in Horner form with fused multiply-adds. Then e^-x * 2^53 = q 2^(53-k)
+// exactly, so trunc() of it is q's 24-bit significand shifted by its binary
+// exponent + 53 - k: integer operations only (a float -> uint64 conversion
+// would run on the FP64 pipe).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float expneg_f32(float x) {
+__device__ __forceinline__ unsigned long long eq5_weight(int shifted_de, float beta) {
+    const float x = __fmul_rn(__int2float_rn(shifted_de), beta);
+    if (!(x <= 40.0f)) return 0ull;
     const float t = __fadd_rn(__fmul_rn(x, 1.44269502f), 0.5f);
     const int k = __float2int_rz(t);
     const float kf = __int2float_rn(k);
     float r = __fmaf_rn(-kf, 0.693145751953125f, x);
     r = __fmaf_rn(-kf, 1.42860677e-06f, r);
     const float y = -r;
-    float q = 1.98412701e-04f;      // 1/7!
+    float q = 1.98412701e-04f;             // 1/7!
     q = __fmaf_rn(q, y, 1.38888892e-03f);  // 1/6!
     q = __fmaf_rn(q, y, 8.33333377e-03f);  // 1/5!
     q = __fmaf_rn(q, y, 4.16666679e-02f);  // 1/4!
@@ -112,13 +128,12 @@ __device__ __forceinline__ float expneg_f32(float x) {
     q = __fmaf_rn(q, y, 0.5f);
     q = __fmaf_rn(q, y, 1.0f);
     q = __fmaf_rn(q, y, 1.0f);
-    return __fmul_rn(q, __int_as_float((127 - k) << 23));
-}
-
-__device__ __forceinline__ unsigned long long eq5_weight(int shifted_de, float beta) {
-    const float x = __fmul_rn(__int2float_rn(shifted_de), beta);
-    if (!(x <= 40.0f)) return 0ull;
-    return __float2ull_rz(__fmul_rn(expneg_f32(x), 9007199254740992.0f));
+    // q in (0.7, 1.5): a normal float; q = mant * 2^(exp - 150).
+    const uint32_t bits = __float_as_uint(q);
+    const int sh = (int)(bits >> 23) - 150 + 53 - k;
+    const unsigned long long mant = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
+    if (sh >= 0) return mant << sh;
+    return sh > -24 ? (mant >> (-sh)) : 0ull;
 }
 
 __device__ __forceinline__ int warp_min(int v) {
@@ -134,17 +149,17 @@ __device__ __forceinline__ long long warp_sum(long long v) {
 }
 
 template <int K>
-__device__ __forceinline__ void load_lane_block(const int32_t *sv, int lane, int (&d)[K]) {
+__device__ __forceinline__ void load_block(const int32_t *sv, int t, int (&d)[K]) {
     if constexpr (K == 1) {
-        d[0] = sv[lane];
+        d[0] = sv[t];
     } else if constexpr (K == 2) {
-        const int2 v = reinterpret_cast<const int2 *>(sv)[lane];
+        const int2 v = reinterpret_cast<const int2 *>(sv)[t];
         d[0] = v.x;
         d[1] = v.y;
     } else {
 #pragma unroll
         for (int h = 0; h < K / 4; ++h) {
-            const int4 v = reinterpret_cast<const int4 *>(sv)[lane * (K / 4) + h];
+            const int4 v = reinterpret_cast<const int4 *>(sv)[t * (K / 4) + h];
             d[4 * h + 0] = v.x;
             d[4 * h + 1] = v.y;
             d[4 * h + 2] = v.z;
@@ -153,17 +168,39 @@ __device__ __forceinline__ void load_lane_block(const int32_t *sv, int lane, int
     }
 }
 
+template <int WPR>
+__device__ __forceinline__ void group_sync(int bar) {
+    if constexpr (WPR == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(32 * WPR) : "memory");
+    }
+}
+
+__device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
+    x.x += u * v.x;
+    x.y += u * v.y;
+    x.z += u * v.z;
+    x.w += u * v.w;
+}
+
 // ---------------------------------------------------------------------------
 // One replica: initial state, table build, sweeps [sweep_begin, sweep_end),
 // write-back. `T` is the replica's influence table (shared or global memory),
 // row stride S; sp = permutation, sh = p-diagonal h[m] = I[m][p(m)],
 // sv = scratch (swap energies in j order, then the rank-1 column factor).
-// MAXK = candidates (and table rows) per lane, a power of two >= n/32.
+// Thread t of the group owns candidates / table rows t + G k, k < MAXK, and
+// weights t*MAXK .. t*MAXK + MAXK - 1. MAXK is a power of two >= n / G.
 // ---------------------------------------------------------------------------
-template <typename DT, int MAXK>
-__device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int lane, const DT *sD,
-                                            const DT *sF, int32_t *T, int32_t *sp, int32_t *sh,
-                                            int32_t *sv) {
+template <typename DT, int MAXK, int WPR>
+__device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, int bar,
+                                            const DT *sD, const DT *sF, int32_t *T, int32_t *sp,
+                                            int32_t *sh, int32_t *sv, GroupScratch *gs) {
+    constexpr int G = 32 * WPR;
+    constexpr int ROWS = WPR * MAXK;       // table rows per lane in the rank-1 update (32-row slots)
+    constexpr int QB = ROWS <= 4 ? 2 : 1;  // table quads per batch of the rank-1 update
+    const int lane = t & 31;
+    const int wg = t >> 5;
     const int n = a.n;
     const int S = a.stride;
     const int npad = (n + 3) & ~3;
@@ -175,24 +212,24 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int lane,
     // word k%4 of Philox(inst, replica, 0xFFFFFFFF, k/4) and index
     // floor(u (k+1) / 2^32).
     if (a.fresh) {
-        for (int q = lane; 4 * q < n; q += 32) {
+        for (int q = t; 4 * q < n; q += G) {
             const uint4 o = philox4x32_10(a.inst, grep, 0xFFFFFFFFu, (uint32_t)q, a.key0, a.key1);
             reinterpret_cast<uint4 *>(sv)[q] = o;
         }
-        for (int m = lane; m < n; m += 32) sp[m] = m;
-        __syncwarp();
-        if (lane == 0) {
+        for (int m = t; m < n; m += G) sp[m] = m;
+        group_sync<WPR>(bar);
+        if (t == 0) {
             for (int k = n - 1; k >= 1; --k) {
                 const int j = (int)__umulhi((uint32_t)sv[k], (uint32_t)(k + 1));
-                const int t = sp[k];
+                const int x = sp[k];
                 sp[k] = sp[j];
-                sp[j] = t;
+                sp[j] = x;
             }
         }
     } else {
-        for (int m = lane; m < n; m += 32) sp[m] = gp[m];
+        for (int m = t; m < n; m += G) sp[m] = gp[m];
     }
-    __syncwarp();
+    group_sync<WPR>(bar);
 
     // ---- influence table, Eq. 2 in the one-term form I[m][c] = sum_j D[m][j] F[c][p(j)]
     // (F symmetric, so row p(j) of F is read contiguously).
@@ -201,44 +238,38 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int lane,
         if (src != T) {
             const int4 *s4 = reinterpret_cast<const int4 *>(src);
             int4 *d4 = reinterpret_cast<int4 *>(T);
-            for (int idx = lane; idx < n * S / 4; idx += 32) d4[idx] = s4[idx];
+            for (int idx = t; idx < n * S / 4; idx += G) d4[idx] = s4[idx];
         }
     } else {
         for (int m = 0; m < n; ++m) {
-            int acc[MAXK];
-#pragma unroll
-            for (int k = 0; k < MAXK; ++k) acc[k] = 0;
             const DT *Dm = sD + m * n;
-            for (int j = 0; j < n; ++j) {
-                const int d = Dm[j];
-                const DT *Fr = sF + sp[j] * n;
-#pragma unroll
-                for (int k = 0; k < MAXK; ++k) {
-                    const int c = lane + 32 * k;
-                    if (c < n) acc[k] += d * (int)Fr[c];
+            for (int c0 = 0; c0 < npad; c0 += G) {
+                const int c = c0 + t;
+                int acc = 0;
+                if (c < n) {
+                    for (int j = 0; j < n; ++j) acc += (int)Dm[j] * (int)sF[sp[j] * n + c];
                 }
-            }
-#pragma unroll
-            for (int k = 0; k < MAXK; ++k) {
-                const int c = lane + 32 * k;
-                if (c < npad) T[m * S + c] = c < n ? acc[k] : 0;
+                if (c < npad) T[m * S + c] = acc;
             }
         }
     }
-    __syncwarp();
+    group_sync<WPR>(bar);
 
     // ---- p-diagonal and energy: E = sum_m I[m][p(m)] (Eq. 1 regrouped)
     long long esum = 0;
-#pragma unroll
-    for (int k = 0; k < MAXK; ++k) {
-        const int m = lane + 32 * k;
-        if (m < n) {
-            const int h = T[m * S + sp[m]];
-            sh[m] = h;
-            esum += h;
-        }
+    for (int m = t; m < n; m += G) {
+        const int h = T[m * S + sp[m]];
+        sh[m] = h;
+        esum += h;
     }
     esum = warp_sum(esum);
+    if constexpr (WPR > 1) {
+        if (lane == 0) gs->wtot[wg] = (unsigned long long)esum;
+        group_sync<WPR>(bar);
+        esum = 0;
+#pragma unroll
+        for (int w = 0; w < WPR; ++w) esum += (long long)gs->wtot[w];
+    }
     long long E, bestE, acc_moves;
     int bsweep;
     if (a.fresh) {
@@ -246,15 +277,15 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int lane,
         bestE = esum;
         bsweep = -1;
         acc_moves = 0;
-        for (int m = lane; m < n; m += 32) gbp[m] = sp[m];
+        for (int m = t; m < n; m += G) gbp[m] = sp[m];
     } else {
         E = a.energy[r];
         bestE = a.best_energy[r];
         bsweep = a.best_sweep[r];
         acc_moves = a.accepted[r];
-        if (E != esum && lane == 0) atomicOr(a.status, 1);
+        if (E != esum && t == 0) atomicOr(a.status, 1);
     }
-    __syncwarp();
+    group_sync<WPR>(bar);
 
     const float beta_pt = (a.mode == 1 && a.sweep_end > a.sweep_begin) ? a.beta[a.rung[r]] : 0.0f;
     const int zero_diag = a.zero_diag;
@@ -274,43 +305,45 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int lane,
                 const int hi = sh[i];
                 const DT *Di = sD + i * n;
                 const DT *Fa = sF + fa * n;
-                const int dii = Di[i];
-                const int faa = Fa[fa];
 
-                // ---- gather: Eq. 3 for every candidate j (lane-interleaved)
+                // ---- gather: Eq. 3 for every candidate j
                 int lmin = 0x7FFFFFFF;
 #pragma unroll
                 for (int k = 0; k < MAXK; ++k) {
-                    const int j = lane + 32 * k;
-                    int d = 0x7FFFFFFF;
+                    const int j = t + G * k;
                     if (j < n) {
                         const int b = sp[j];
-                        const int row_ib = T[i * S + b];
-                        const int col_ja = T[j * S + fa];
                         const int dij = Di[j];
                         const int fab = Fa[b];
-                        d = 2 * (row_ib - hi + col_ja - sh[j]);
+                        int d = 2 * (T[i * S + b] - hi + T[j * S + fa] - sh[j]);
                         if (zero_diag)
                             d += 4 * dij * fab;
                         else
-                            d += (dii + (int)sD[j * n + j] - 2 * dij) * (faa + (int)sF[b * n + b] - 2 * fab);
+                            d += ((int)Di[i] + (int)sD[j * n + j] - 2 * dij) *
+                                 ((int)Fa[fa] + (int)sF[b * n + b] - 2 * fab);
                         if (j == i) d = 0;
                         sv[j] = d;
+                        lmin = min(lmin, d);
                     }
-                    lmin = min(lmin, d);
                 }
-                const int dmin = warp_min(lmin);
-                __syncwarp();
+                int dmin = warp_min(lmin);
+                if constexpr (WPR > 1) {
+                    if (lane == 0) gs->wmin[wg] = dmin;
+                    group_sync<WPR>(bar);
+#pragma unroll
+                    for (int w = 0; w < WPR; ++w) dmin = min(dmin, gs->wmin[w]);
+                } else {
+                    __syncwarp();
+                }
 
-                // ---- sample: lane-contiguous weights, 64-bit prefix sums
+                // ---- sample: thread-contiguous weights, 64-bit prefix sums
                 int dc[MAXK];
-                load_lane_block<MAXK>(sv, lane, dc);
+                load_block<MAXK>(sv, t, dc);
                 unsigned long long pre[MAXK];
                 unsigned long long lsum = 0;
 #pragma unroll
                 for (int k = 0; k < MAXK; ++k) {
-                    const int j = lane * MAXK + k;
-                    if (j < n) lsum += eq5_weight(dc[k] - dmin, beta);
+                    if (t * MAXK + k < n) lsum += eq5_weight(dc[k] - dmin, beta);
                     pre[k] = lsum;
                 }
                 unsigned long long incl = lsum;
@@ -319,84 +352,139 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int lane,
                     const unsigned long long y = __shfl_up_sync(kFull, incl, o);
                     if (lane >= o) incl += y;
                 }
-                const unsigned long long total = __shfl_sync(kFull, incl, 31);
+                unsigned long long total = __shfl_sync(kFull, incl, 31);
+                if constexpr (WPR > 1) {
+                    if (lane == 31) gs->wtot[wg] = incl;
+                    group_sync<WPR>(bar);
+                    unsigned long long off = 0;
+                    total = 0;
+#pragma unroll
+                    for (int w = 0; w < WPR; ++w) {
+                        const unsigned long long v = gs->wtot[w];
+                        if (w < wg) off += v;
+                        total += v;
+                    }
+                    incl += off;
+                }
                 const unsigned long long excl = incl - lsum;
-                const unsigned long long t = __umul64hi(draw, total);
-                const bool own = (t >= excl) && (t < incl);
-                const unsigned ball = __ballot_sync(kFull, own);
-                const int src = __ffs(ball) - 1;
+                const unsigned long long tdraw = __umul64hi(draw, total);
+                const bool own = (tdraw >= excl) && (tdraw < incl);
                 int jloc = 0, dsel = 0;
                 if (own) {
                     int kk = MAXK - 1;
 #pragma unroll
                     for (int k = MAXK - 1; k >= 0; --k)
-                        if (excl + pre[k] > t) kk = k;
+                        if (excl + pre[k] > tdraw) kk = k;
 #pragma unroll
                     for (int k = 0; k < MAXK; ++k)
                         if (k == kk) dsel = dc[k];
-                    jloc = lane * MAXK + kk;
+                    jloc = t * MAXK + kk;
                 }
-                const int js = __shfl_sync(kFull, jloc, src);
-                const int dstar = __shfl_sync(kFull, dsel, src);
-                __syncwarp();
+                int js, dstar;
+                if constexpr (WPR > 1) {
+                    if (own) {
+                        gs->sel_j = jloc;
+                        gs->sel_d = dsel;
+                    }
+                    group_sync<WPR>(bar);
+                    js = gs->sel_j;
+                    dstar = gs->sel_d;
+                } else {
+                    const int src = __ffs(__ballot_sync(kFull, own)) - 1;
+                    js = __shfl_sync(kFull, jloc, src);
+                    dstar = __shfl_sync(kFull, dsel, src);
+                    __syncwarp();
+                }
                 if (js == i) continue;
 
-                // ---- apply the swap i <-> js: rank-1 update of the table
+                // ---- apply the swap i <-> js: rank-1 update of the table.
+                // Lane l of every warp owns rows l + 32 k; warp w of the group
+                // owns column quads w, w + WPR, ... so each warp reads each
+                // column-factor quad once.
                 const int fb = sp[js];
                 const DT *Fb = sF + fb * n;
                 const DT *Dj = sD + js * n;
-                for (int c = lane; c < npad; c += 32) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
-                int u[MAXK];
+                for (int c = t; c < npad; c += G) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
+                int u[ROWS];
 #pragma unroll
-                for (int k = 0; k < MAXK; ++k) {
+                for (int k = 0; k < ROWS; ++k) {
                     const int m = lane + 32 * k;
                     u[k] = m < n ? (int)Di[m] - (int)Dj[m] : 0;
                 }
-                __syncwarp();
+                // old I[i][fb] and I[js][fa], for the two p-diagonal entries that move
+                int tib = 0, tja = 0;
+                if (t == 0) {
+                    tib = T[i * S + fb];
+                    tja = T[js * S + fa];
+                }
+                group_sync<WPR>(bar);
                 const int4 *v4 = reinterpret_cast<const int4 *>(sv);
-#pragma unroll 2
-                for (int cq = 0; cq < npad / 4; ++cq) {
+                const int nq = npad / 4;
+                int cq = wg;
+                for (; cq + (QB - 1) * WPR < nq; cq += QB * WPR) {
+                    int4 vq[QB];
+#pragma unroll
+                    for (int b = 0; b < QB; ++b) vq[b] = v4[cq + b * WPR];
+                    int4 x[ROWS][QB];
+#pragma unroll
+                    for (int k = 0; k < ROWS; ++k) {
+                        if (lane + 32 * k < n) {
+                            const int4 *row = reinterpret_cast<const int4 *>(T + (lane + 32 * k) * S) + cq;
+#pragma unroll
+                            for (int b = 0; b < QB; ++b) x[k][b] = row[b * WPR];
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < ROWS; ++k) {
+                        if (lane + 32 * k < n) {
+                            int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+#pragma unroll
+                            for (int b = 0; b < QB; ++b) {
+                                add_scaled(x[k][b], u[k], vq[b]);
+                                row[b * WPR] = x[k][b];
+                            }
+                        }
+                    }
+                }
+                for (; cq < nq; cq += WPR) {
                     const int4 vq = v4[cq];
 #pragma unroll
-                    for (int k = 0; k < MAXK; ++k) {
-                        const int m = lane + 32 * k;
-                        if (m < n) {
-                            int4 *row = reinterpret_cast<int4 *>(T + m * S) + cq;
+                    for (int k = 0; k < ROWS; ++k) {
+                        if (lane + 32 * k < n) {
+                            int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
                             int4 x = *row;
-                            x.x += u[k] * vq.x;
-                            x.y += u[k] * vq.y;
-                            x.z += u[k] * vq.z;
-                            x.w += u[k] * vq.w;
+                            add_scaled(x, u[k], vq);
                             *row = x;
                         }
                     }
                 }
-                __syncwarp();
-                if (lane == 0) {
+                // p-diagonal h[m] = I[m][p(m)] under the new table and permutation:
+                // h[m] += u_m v[p(m)] where p(m) is unchanged; the two moved
+                // entries from the old I[i][fb], I[js][fa]. Thread 0 writes the
+                // new sp[i], sp[js]; those two are not read here.
+                for (int m = t; m < n; m += G)
+                    if (m != i && m != js) sh[m] += ((int)Di[m] - (int)Dj[m]) * sv[sp[m]];
+                if (t == 0) {
                     sp[i] = fb;
                     sp[js] = fa;
-                }
-                __syncwarp();
-#pragma unroll
-                for (int k = 0; k < MAXK; ++k) {
-                    const int m = lane + 32 * k;
-                    if (m < n) sh[m] = T[m * S + sp[m]];
+                    sh[i] = tib + ((int)Di[i] - (int)Dj[i]) * sv[fb];
+                    sh[js] = tja + ((int)Di[js] - (int)Dj[js]) * sv[fa];
                 }
                 E += dstar;
                 acc_moves += 1;
                 if (E < bestE) {
                     bestE = E;
                     bsweep = s;
-                    for (int m = lane; m < n; m += 32) gbp[m] = sp[m];
+                    for (int m = t; m < n; m += G) gbp[m] = m == i ? fb : (m == js ? fa : sp[m]);
                 }
-                __syncwarp();
+                group_sync<WPR>(bar);
             }
         }
     }
 
     // ---- write back
-    for (int m = lane; m < n; m += 32) gp[m] = sp[m];
-    if (lane == 0) {
+    for (int m = t; m < n; m += G) gp[m] = sp[m];
+    if (t == 0) {
         a.energy[r] = E;
         a.best_energy[r] = bestE;
         a.best_sweep[r] = bsweep;
@@ -407,27 +495,38 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int lane,
         if (dst != T) {
             const int4 *s4 = reinterpret_cast<const int4 *>(T);
             int4 *d4 = reinterpret_cast<int4 *>(dst);
-            for (int idx = lane; idx < n * S / 4; idx += 32) d4[idx] = s4[idx];
+            for (int idx = t; idx < n * S / 4; idx += G) d4[idx] = s4[idx];
         }
     }
     if (a.dump) {
         int32_t *dst = a.dump + (size_t)r * n * n;
-        for (int idx = lane; idx < n * n; idx += 32) dst[idx] = T[(idx / n) * S + idx % n];
+        for (int idx = t; idx < n * n; idx += G) dst[idx] = T[(idx / n) * S + idx % n];
     }
-    __syncwarp();
+    group_sync<WPR>(bar);
 }
 
-template <int MAXK>
+// Largest CTA each instantiation is compiled for; it caps the registers per
+// thread at 65536 / bound, so it is set per shape from its register needs.
+__host__ __device__ constexpr int sweep_bound(int maxk, int wpr) {
+    return wpr == 1 ? (maxk == 1 ? 1024 : maxk == 2 ? 512 : maxk == 4 ? 384 : 128)
+         : wpr == 2 ? (maxk == 1 ? 1024 : maxk == 2 ? 512 : 384)
+         : wpr == 4 ? (maxk == 1 ? 640 : 512)
+         : 512;
+}
+
+template <int MAXK, int WPR>
 struct SweepBounds {
-    static constexpr int threads = MAXK == 1 ? 1024 : (MAXK == 2 ? 512 : (MAXK == 4 ? 384 : 128));
+    static constexpr int threads = sweep_bound(MAXK, WPR);
 };
 
-template <typename DT, int MAXK, bool TSMEM>
-__global__ void __launch_bounds__(SweepBounds<MAXK>::threads) sweep_kernel(const SweepArgs a) {
+template <typename DT, int MAXK, int WPR, bool TSMEM>
+__global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int G = 32 * WPR;
     const int n = a.n;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const int grp = threadIdx.x / G;
+    const int t = threadIdx.x % G;
+    const int bar = 1 + grp;  // named barrier of this group (WPR > 1); 0 is __syncthreads
     DT *sD = reinterpret_cast<DT *>(smem);
     DT *sF = sD + n * n;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -435,40 +534,50 @@ __global__ void __launch_bounds__(SweepBounds<MAXK>::threads) sweep_kernel(const
         sF[idx] = static_cast<DT>(a.F[idx]);
     }
     __syncthreads();
-    unsigned char *wb = smem + a.df_bytes + (size_t)warp * a.warp_bytes;
+    unsigned char *gb = smem + a.df_bytes + (size_t)grp * a.group_bytes;
     const int npad = (n + 3) & ~3;
-    int32_t *sT = reinterpret_cast<int32_t *>(wb);
-    int32_t *sp = reinterpret_cast<int32_t *>(wb + (TSMEM ? (size_t)n * a.stride * 4 : 0));
+    GroupScratch *gs = reinterpret_cast<GroupScratch *>(gb);
+    unsigned char *body = gb + kScratchBytes;
+    int32_t *sT = reinterpret_cast<int32_t *>(body);
+    int32_t *sp = reinterpret_cast<int32_t *>(body + (TSMEM ? (size_t)n * a.stride * 4 : 0));
     int32_t *sh = sp + npad;
     int32_t *sv = sh + npad;
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.queue, 1);
-        item = __shfl_sync(kFull, item, 0);
+        if (t == 0) gs->item = atomicAdd(a.queue, 1);
+        group_sync<WPR>(bar);
+        const int item = gs->item;
         if (item >= a.replicas) break;
         if constexpr (TSMEM) {
-            run_replica<DT, MAXK>(a, item, lane, sD, sF, sT, sp, sh, sv);
+            run_replica<DT, MAXK, WPR>(a, item, t, bar, sD, sF, sT, sp, sh, sv, gs);
         } else {
-            run_replica<DT, MAXK>(a, item, lane, sD, sF, a.tables + (size_t)item * n * a.stride, sp,
-                                  sh, sv);
+            run_replica<DT, MAXK, WPR>(a, item, t, bar, sD, sF, a.tables + (size_t)item * n * a.stride,
+                                       sp, sh, sv, gs);
         }
     }
 }
 
 // Host-side entry points, one per storage type of D and F (defined in
-// pdit_sweep_i8.cu, pdit_sweep_i16.cu, pdit_sweep_i32.cu).
-// maxk in {1, 2, 4, 8}. Return a cudaError_t value.
+// pdit_sweep_i8.cu, pdit_sweep_i16.cu, pdit_sweep_i32.cu). Return a
+// cudaError_t value; cudaErrorInvalidValue for a shape with no kernel.
 template <typename DT>
-int sweep_blocks_per_sm(int maxk, bool tsmem, int threads, size_t smem, int *blocks);
+int sweep_blocks_per_sm(int maxk, int wpr, bool tsmem, int threads, size_t smem, int *blocks);
 template <typename DT>
-int sweep_launch(int maxk, bool tsmem, const SweepArgs &a, int grid, int threads, size_t smem,
+int sweep_launch(int maxk, int wpr, bool tsmem, const SweepArgs &a, int grid, int threads, size_t smem,
                  cudaStream_t stream);
 
+// Shapes with a compiled kernel: (MAXK, WPR) with 32 * WPR * MAXK in
+// {32, 64, 128, 256}; the global-table variant only for 256.
+#define PDIT_SWEEP_SHAPES(X)                                                                     \
+    X(1, 1, true) X(2, 1, true) X(1, 2, true) X(4, 1, true) X(2, 2, true) X(1, 4, true)          \
+    X(8, 1, true) X(4, 2, true) X(2, 4, true) X(1, 8, true)                                      \
+    X(8, 1, false) X(4, 2, false) X(2, 4, false) X(1, 8, false)
+
 #define PDIT_INSTANTIATE_SWEEP(DT)                                                               \
-    template <int MAXK, bool TSMEM>                                                              \
+    template <int MAXK, int WPR, bool TSMEM>                                                     \
     static int sweep_one(const SweepArgs &a, int grid, int threads, size_t smem,                \
                          cudaStream_t st, int *blocks, bool query) {                             \
-        auto fn = sweep_kernel<DT, MAXK, TSMEM>;                                                 \
+        auto fn = sweep_kernel<DT, MAXK, WPR, TSMEM>;                                            \
+        if (threads > SweepBounds<MAXK, WPR>::threads) return (int)cudaErrorInvalidValue;        \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                              (int)smem);                                         \
         if (e != cudaSuccess) return (int)e;                                                     \
@@ -477,27 +586,26 @@ int sweep_launch(int maxk, bool tsmem, const SweepArgs &a, int grid, int threads
         fn<<<grid, threads, smem, st>>>(a);                                                      \
         return (int)cudaGetLastError();                                                          \
     }                                                                                            \
-    static int sweep_dispatch(int maxk, bool tsmem, const SweepArgs &a, int grid, int threads,   \
-                              size_t smem, cudaStream_t st, int *blocks, bool query) {           \
-        switch (maxk * 2 + (tsmem ? 1 : 0)) {                                                    \
-        case 3: return sweep_one<1, true>(a, grid, threads, smem, st, blocks, query);            \
-        case 5: return sweep_one<2, true>(a, grid, threads, smem, st, blocks, query);            \
-        case 9: return sweep_one<4, true>(a, grid, threads, smem, st, blocks, query);            \
-        case 17: return sweep_one<8, true>(a, grid, threads, smem, st, blocks, query);           \
-        case 8: return sweep_one<4, false>(a, grid, threads, smem, st, blocks, query);           \
-        case 16: return sweep_one<8, false>(a, grid, threads, smem, st, blocks, query);          \
-        default: return (int)cudaErrorInvalidValue;                                              \
-        }                                                                                        \
+    static int sweep_dispatch(int maxk, int wpr, bool tsmem, const SweepArgs &a, int grid,       \
+                              int threads, size_t smem, cudaStream_t st, int *blocks,            \
+                              bool query) {                                                      \
+        PDIT_SWEEP_SHAPES(PDIT_CASE)                                                             \
+        return (int)cudaErrorInvalidValue;                                                       \
     }                                                                                            \
     template <>                                                                                  \
-    int sweep_blocks_per_sm<DT>(int maxk, bool tsmem, int threads, size_t smem, int *blocks) {   \
+    int sweep_blocks_per_sm<DT>(int maxk, int wpr, bool tsmem, int threads, size_t smem,         \
+                                int *blocks) {                                                   \
         SweepArgs dummy{};                                                                       \
-        return sweep_dispatch(maxk, tsmem, dummy, 0, threads, smem, nullptr, blocks, true);      \
+        return sweep_dispatch(maxk, wpr, tsmem, dummy, 0, threads, smem, nullptr, blocks, true); \
     }                                                                                            \
     template <>                                                                                  \
-    int sweep_launch<DT>(int maxk, bool tsmem, const SweepArgs &a, int grid, int threads,        \
-                         size_t smem, cudaStream_t st) {                                         \
-        return sweep_dispatch(maxk, tsmem, a, grid, threads, smem, st, nullptr, false);          \
+    int sweep_launch<DT>(int maxk, int wpr, bool tsmem, const SweepArgs &a, int grid,            \
+                         int threads, size_t smem, cudaStream_t st) {                            \
+        return sweep_dispatch(maxk, wpr, tsmem, a, grid, threads, smem, st, nullptr, false);     \
     }
+
+#define PDIT_CASE(MK, W, TS)                                                                     \
+    if (maxk == MK && wpr == W && tsmem == TS)                                                   \
+        return sweep_one<MK, W, TS>(a, grid, threads, smem, st, blocks, query);
 
 }  // namespace pdit

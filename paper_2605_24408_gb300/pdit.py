@@ -103,6 +103,10 @@ def lib():
     L.pdit_beta_max.restype = ctypes.c_int
     L.pdit_beta_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]
     L.pdit_beta_schedule.restype = ctypes.c_int
+    L.pdit_set_warps_per_replica.argtypes = [vp, ctypes.c_int]
+    L.pdit_set_warps_per_replica.restype = ctypes.c_int
+    L.pdit_launch_shape.argtypes = [vp, ctypes.c_int, vp]
+    L.pdit_launch_shape.restype = ctypes.c_int
     L.pdit_strerror.argtypes = [ctypes.c_int]
     L.pdit_strerror.restype = ctypes.c_char_p
     L.pdit_last_error.argtypes = []
@@ -196,6 +200,17 @@ def pdit_anneal_host_ptrs(q: Qap, replicas: int, beta_ptr: int, sweeps: int, see
     return lib().pdit_anneal(q.handle, replicas, ctypes.c_void_p(beta_ptr), sweeps,
                              seed & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(perm_ptr),
                              ctypes.c_void_p(cost_ptr))
+
+
+def pdit_set_warps_per_replica(q: Qap, wpr: int):
+    _check(lib().pdit_set_warps_per_replica(q.handle, wpr), "pdit_set_warps_per_replica")
+
+
+def pdit_launch_shape(q: Qap, replicas: int) -> dict:
+    out = np.zeros(6, dtype=np.int32)
+    _check(lib().pdit_launch_shape(q.handle, replicas, _ptr(out)), "pdit_launch_shape")
+    return dict(zip(["warps_per_replica", "candidates_per_thread", "replicas_per_cta", "ctas",
+                     "tables_in_smem", "smem_bytes"], (int(x) for x in out)))
 
 
 def pdit_beta_max(q: Qap) -> float:

@@ -30,9 +30,11 @@ def P():
     return pdit
 
 
-def gpu_run(D, F, beta, sweeps, seed, R, tables=False, **kw):
+def gpu_run(D, F, beta, sweeps, seed, R, tables=False, wpr=0, **kw):
     p = P()
     with p.Qap(D, F) as q:
+        if wpr:
+            p.pdit_set_warps_per_replica(q, wpr)
         dbeta = torch.from_numpy(np.ascontiguousarray(beta, np.float32)).cuda() if len(beta) else \
             torch.zeros(1, dtype=torch.float32, device="cuda")
         out = p.anneal_device(q, R, dbeta, sweeps, seed, per_replica=True, tables=tables, **kw)
@@ -121,12 +123,26 @@ def test_sizes_dense(n):
     check_equal(g, r, tables=True)
 
 
-@pytest.mark.parametrize("n,lo,hi,diag", [(20, -9, 9, True), (40, 0, 300, False), (40, -300, 300, True),
-                                          (70, 0, 40000, False), (24, -2000, 2000, True)])
-def test_value_ranges_signs_and_diagonals(n, lo, hi, diag):
+@pytest.mark.parametrize("n,wpr", [(30, 1), (40, 1), (40, 2), (100, 1), (100, 2), (100, 4), (129, 1),
+                                   (129, 2), (129, 4), (129, 8), (190, 8), (256, 1), (256, 2), (256, 4),
+                                   (256, 8)])
+def test_every_thread_mapping(n, wpr):
+    """Every warps-per-replica shape gives the oracle's results."""
+    D, F = G.dense_instance(n, seed=n + 7)
+    sweeps = 5
+    beta = schedule(D, F, "linear", sweeps) * np.float32(0.5)
+    g = gpu_run(D, F, beta, sweeps, 21, 4, tables=True, wpr=wpr)
+    r = O.anneal(D, F, beta, sweeps, 21, 0, 4, threads=4, tables=True)
+    check_equal(g, r, tables=True)
+
+
+@pytest.mark.parametrize("n,lo,hi,fmax,diag", [(20, -9, 9, 9, True), (40, 0, 300, 50, False),
+                                               (40, -300, 300, 50, True), (70, 0, 40000, 20, False),
+                                               (24, -2000, 2000, 50, True)])
+def test_value_ranges_signs_and_diagonals(n, lo, hi, fmax, diag):
     """int8 / int16 / int32 staging of D and F, negative entries, nonzero diagonals."""
     D = G.random_symmetric(n, lo, hi, seed=n + 1, tag=1, diag=diag)
-    F = G.random_symmetric(n, max(lo, -50), min(hi, 50), seed=n + 2, tag=2, diag=diag)
+    F = G.random_symmetric(n, max(lo, -fmax), fmax, seed=n + 2, tag=2, diag=diag)
     bm = O.beta_max(D, F)
     beta = O.beta_schedule("linear", 15, bm)
     g = gpu_run(D, F, beta, 15, 3, 6, tables=True)
