@@ -197,6 +197,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--wpr", type=int, default=0,
                     help="warps per replica (0: the library's choice)")
+    ap.add_argument("--pk", type=int, default=0,
+                    help="accepted swaps held before a table rewrite (0: the library's choice)")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="override the workload's sweep count (smaller cases for profiling)")
     args = ap.parse_args()
@@ -232,6 +234,8 @@ def main():
     q = P.Qap(D, F)
     if args.wpr:
         P.pdit_set_warps_per_replica(q, args.wpr)
+    if args.pk:
+        P.pdit_set_pending_swaps(q, args.pk)
     shape = P.pdit_launch_shape(q, replicas)
     beta = P.pdit_beta_schedule(kind, sweeps, P.pdit_beta_max(q))
     dev = torch.device("cuda", local)
@@ -351,9 +355,10 @@ def main():
                    "reasons": clk.get("reasons"), "samples": clk.get("samples")},
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if peak else None, "traffic": traffic,
-                     "kernel": "sweep_kernel<int8,%d,%d,%s>" % (shape["candidates_per_thread"],
-                                                                shape["warps_per_replica"],
-                                                                "smem" if shape["tables_in_smem"] else "global"),
+                     "kernel": "sweep_kernel<int8,%d,%d,%s,%d>" % (shape["candidates_per_thread"],
+                                                                   shape["warps_per_replica"],
+                                                                   "smem" if shape["tables_in_smem"] else "global",
+                                                                   shape["pending_swaps"]),
                      "bytes_per_update": bpu,
                      "peak_source": "derived: %d SMs x %d B/clk x median SM clock under load (%s MHz)"
                                     % (props.multi_processor_count, SMEM_BYTES_PER_CLK, sm_mhz)},

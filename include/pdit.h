@@ -96,9 +96,23 @@ int pdit_set_warps_per_replica(pdit_qap *h, int wpr);
  * would use: shape[0] warps per replica, [1] candidates per thread, [2]
  * replicas per CTA, [3] CTAs, [4] 1 if the influence tables live in shared
  * memory (0: global memory), [5] dynamic shared memory bytes per CTA.
- * `shape` is a host array of 6 ints. Errors: PDIT_EINVAL, PDIT_ENOTSUP.
+ * [6] swaps held before the influence table is rewritten (1 = after each).
+ * `shape` is a host array of 7 ints. Errors: PDIT_EINVAL, PDIT_ENOTSUP.
  */
 int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape);
+
+/*
+ * pdit_set_pending_swaps -- table-update batching of later calls on this
+ * handle: k = 1 rewrites the influence table after every accepted swap
+ * (the rank-1 update implied by Eq. 2); k = 4 keeps up to four accepted
+ * swaps as pending rank-1 terms that every query adds in, and rewrites the
+ * table once per four swaps (a rank-4 update). 0 restores the built-in
+ * choice. k = 4 needs max - min <= 127 over the entries of D and of F (so
+ * every swap factor fits a signed byte) and the tables in shared memory
+ * (PDIT_ENOTSUP otherwise, at the next call). Results do not depend on k.
+ * Errors: PDIT_EINVAL.
+ */
+int pdit_set_pending_swaps(pdit_qap *h, int k);
 
 /*
  * pdit_anneal -- synchronous annealed p-dit sweep on HOST buffers.

@@ -19,6 +19,7 @@ struct pdit_qap {
     size_t smem_optin = 0;
     int dt_bytes = 4;       // storage of D and F in shared memory: 1, 2 or 4 bytes
     int zero_diag = 0;
+    int packed_ok = 0;      // max-min of D and of F <= 127: swap factors fit int8
     std::vector<int32_t> hD, hF;
     int32_t *dD = nullptr, *dF = nullptr;
     // owned by the handle, grown on demand
@@ -31,6 +32,7 @@ struct pdit_qap {
     int32_t *dstatus = nullptr;
     cudaStream_t stream = nullptr;
     int force_wpr = 0;      // warps per replica; 0 = chosen per launch
+    int force_pk = 0;       // pending swaps before a table rewrite; 0 = chosen per launch
 };
 
 namespace {
@@ -67,46 +69,65 @@ int cover_for(int n) {
 }
 
 struct Plan {
-    int maxk = 1, wpr = 1;
+    int maxk = 1, wpr = 1, pk = 1;
     bool tsmem = true;
-    int stride = 0;
+    int stride = 0, sv_len = 0;
     size_t df_bytes = 0, group_bytes = 0, smem = 0;
     int groups = 1, threads = 32, grid = 1;
 };
 
 
 int sweep_blocks(int dt, const Plan &p, int *blocks) {
-    if (dt == 1) return pdit::sweep_blocks_per_sm<int8_t>(p.maxk, p.wpr, p.tsmem, p.threads, p.smem, blocks);
-    if (dt == 2) return pdit::sweep_blocks_per_sm<int16_t>(p.maxk, p.wpr, p.tsmem, p.threads, p.smem, blocks);
-    return pdit::sweep_blocks_per_sm<int32_t>(p.maxk, p.wpr, p.tsmem, p.threads, p.smem, blocks);
+    if (dt == 1) return pdit::sweep_blocks_per_sm<int8_t>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
+    if (dt == 2) return pdit::sweep_blocks_per_sm<int16_t>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
+    return pdit::sweep_blocks_per_sm<int32_t>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
 }
 
 int sweep_launch(int dt, const Plan &p, const pdit::SweepArgs &a, cudaStream_t st) {
-    if (dt == 1) return pdit::sweep_launch<int8_t>(p.maxk, p.wpr, p.tsmem, a, p.grid, p.threads, p.smem, st);
-    if (dt == 2) return pdit::sweep_launch<int16_t>(p.maxk, p.wpr, p.tsmem, a, p.grid, p.threads, p.smem, st);
-    return pdit::sweep_launch<int32_t>(p.maxk, p.wpr, p.tsmem, a, p.grid, p.threads, p.smem, st);
+    if (dt == 1) return pdit::sweep_launch<int8_t>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
+    if (dt == 2) return pdit::sweep_launch<int16_t>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
+    return pdit::sweep_launch<int32_t>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
 }
 
-// Shared-memory slice of one replica group for a given shape.
-size_t group_bytes_for(int n, int stride, int cover, bool tsmem) {
+// Scratch-vector length (int32 entries) of a group.
+int sv_len_for(int stride, int cover) { return std::max(stride, cover); }
+
+// Shared-memory slice of one replica group for a given shape: scratch
+// struct, table (if in shared memory), p, h, the scratch vector, and the
+// packed pending swap factors (int8 x 4 per word) when pk > 1.
+size_t group_bytes_for(int n, int stride, int cover, bool tsmem, int pk) {
     const size_t npad = (size_t)((n + 3) & ~3);
-    const size_t svn = std::max((size_t)stride, (size_t)cover);
-    const size_t vec = 4 * (2 * npad + svn);
+    const size_t vec = 4 * (2 * npad + (size_t)sv_len_for(stride, cover));
     const size_t table = tsmem ? (size_t)4 * n * stride : 0;
-    return align_up(pdit::kScratchBytes + table + vec, 16);
+    const size_t ring = pk > 1 ? (size_t)8 * npad : 0;  // packed u and v words
+    return align_up(pdit::kScratchBytes + table + vec + ring, 16);
 }
 
 // Launch shape for `replicas` chains of an n-location instance. `wpr` = warps
 // per replica (0: choose).
-int make_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
+int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p) {
     const int n = h->n;
     const int cover = cover_for(n);
     p->stride = table_stride(n);
+    p->sv_len = sv_len_for(p->stride, cover);
     p->df_bytes = align_up((size_t)2 * n * n * h->dt_bytes, 16);
     const size_t budget = h->smem_optin;
-    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true) <= budget;
+    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1) <= budget;
     if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;
-    p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem);
+    const bool defer_ok = p->tsmem && h->packed_ok;
+    if (pk != 0 && pk != 1 && pk != 4) return PDIT_EINVAL;
+    if (pk == 4 && !defer_ok) return PDIT_ENOTSUP;
+    if (pk == 0) {
+        // Defer table rewrites when the ring costs no replica slot.
+        pk = 1;
+        if (defer_ok) {
+            const size_t g1 = group_bytes_for(n, p->stride, cover, true, 1);
+            const size_t g4 = group_bytes_for(n, p->stride, cover, true, 4);
+            if ((budget - p->df_bytes) / g4 == (budget - p->df_bytes) / g1) pk = 4;
+        }
+    }
+    p->pk = pk;
+    p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk);
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
     const int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
     if (wpr <= 0) {
@@ -309,11 +330,16 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     *out = nullptr;
     if (n < 2 || n > PDIT_N_MAX || !D || !F) return PDIT_EINVAL;
     int64_t maxd = 0, maxf = 0;
+    int64_t dlo = D[0], dhi = D[0], flo = F[0], fhi = F[0];
     bool zd = true;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
             const int32_t d = D[(size_t)i * n + j], f = F[(size_t)i * n + j];
             if (d != D[(size_t)j * n + i] || f != F[(size_t)j * n + i]) return PDIT_EINVAL;
+            dlo = std::min<int64_t>(dlo, d);
+            dhi = std::max<int64_t>(dhi, d);
+            flo = std::min<int64_t>(flo, f);
+            fhi = std::max<int64_t>(fhi, f);
             maxd = std::max<int64_t>(maxd, std::llabs((long long)d));
             maxf = std::max<int64_t>(maxf, std::llabs((long long)f));
             if (i == j && (d != 0 || f != 0)) zd = false;
@@ -325,6 +351,7 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     if (!h) return PDIT_ENOMEM;
     h->n = n;
     h->zero_diag = zd ? 1 : 0;
+    h->packed_ok = (dhi - dlo <= 127 && fhi - flo <= 127) ? 1 : 0;
     const int64_t mx = std::max(maxd, maxf);
     h->dt_bytes = mx <= 127 ? 1 : (mx <= 32767 ? 2 : 4);
     h->hD.assign(D, D + (size_t)n * n);
@@ -377,7 +404,7 @@ int pdit_set_warps_per_replica(pdit_qap *h, int wpr) {
 int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape) {
     if (!h || replicas < 1 || !shape) return PDIT_EINVAL;
     Plan p;
-    const int rc = make_plan(h, replicas, h->force_wpr, &p);
+    const int rc = make_plan(h, replicas, h->force_wpr, h->force_pk, &p);
     if (rc) return rc;
     shape[0] = p.wpr;
     shape[1] = p.maxk;
@@ -385,13 +412,20 @@ int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape) {
     shape[3] = p.grid;
     shape[4] = p.tsmem ? 1 : 0;
     shape[5] = (int)p.smem;
+    shape[6] = p.pk;
+    return PDIT_OK;
+}
+
+int pdit_set_pending_swaps(pdit_qap *h, int k) {
+    if (!h || (k != 0 && k != 1 && k != 4)) return PDIT_EINVAL;
+    h->force_pk = k;
     return PDIT_OK;
 }
 
 size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o) {
     if (!h || !o || o->replicas < 1) return 0;
     Plan p;
-    if (make_plan(h, o->replicas, h->force_wpr, &p) != PDIT_OK) return 0;
+    if (make_plan(h, o->replicas, h->force_wpr, h->force_pk, &p) != PDIT_OK) return 0;
     return carve(h, o, p, nullptr).bytes;
 }
 
@@ -399,7 +433,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     int rc = validate_opts(h, o);
     if (rc) return rc;
     Plan plan;
-    rc = make_plan(h, o->replicas, h->force_wpr, &plan);
+    rc = make_plan(h, o->replicas, h->force_wpr, h->force_pk, &plan);
     if (rc) return rc;
     const size_t need = carve(h, o, plan, nullptr).bytes;
     char *base = (char *)o->workspace;
@@ -459,6 +493,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.status = w.status;
     a.df_bytes = plan.df_bytes;
     a.group_bytes = plan.group_bytes;
+    a.sv_len = plan.sv_len;
 
     // Segments: the whole range in anneal mode; exchange periods in PT mode.
     bool first = true;

@@ -62,6 +62,7 @@ struct SweepArgs {
     // launch shape
     size_t df_bytes;       // bytes of staged D and F (16-byte multiple)
     size_t group_bytes;    // bytes of one group's slice
+    int sv_len;            // int32 entries of the scratch vector (multiple of 4)
 };
 
 // Per-group scratch for cross-warp reductions and broadcasts.
@@ -189,13 +190,16 @@ __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
 // write-back. `T` is the replica's influence table (shared or global memory),
 // row stride S; sp = permutation, sh = p-diagonal h[m] = I[m][p(m)],
 // sv = scratch (swap energies in j order, then the rank-1 column factor).
-// Thread t of the group owns candidates / table rows t + G k, k < MAXK, and
-// weights t*MAXK .. t*MAXK + MAXK - 1. MAXK is a power of two >= n / G.
+// Thread t of the group owns candidates t + G k, k < MAXK, and weights
+// t*MAXK .. t*MAXK + MAXK - 1; MAXK is a power of two >= n / G. In table
+// updates lane l of each warp owns rows l + 32 k. PK = pending swaps held
+// before the table is rewritten (1 = immediate rank-1 updates).
 // ---------------------------------------------------------------------------
-template <typename DT, int MAXK, int WPR>
+template <typename DT, int MAXK, int WPR, int PK>
 __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, int bar,
                                             const DT *sD, const DT *sF, int32_t *T, int32_t *sp,
-                                            int32_t *sh, int32_t *sv, GroupScratch *gs) {
+                                            int32_t *sh, int32_t *sv, uint32_t *upk,
+                                            uint32_t *vpk, GroupScratch *gs) {
     constexpr int G = 32 * WPR;
     constexpr int ROWS = WPR * MAXK;       // table rows per lane in the rank-1 update (32-row slots)
     constexpr int QB = ROWS <= 4 ? 2 : 1;  // table quads per batch of the rank-1 update
@@ -289,6 +293,50 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
 
     const float beta_pt = (a.mode == 1 && a.sweep_end > a.sweep_begin) ? a.beta[a.rung[r]] : 0.0f;
     const int zero_diag = a.zero_diag;
+    const int nq = npad / 4;
+
+    // Deferred table updates (PK = 4): the influence table is
+    //   I = T + sum_{q < np} u_q (x) v_q,  u_q[m] = D[i_q][m] - D[j_q][m],
+    //   v_q[c] = F[b_q][c] - F[a_q][c]
+    // for the np <= 4 accepted swaps (i_q <-> j_q, facilities a_q, b_q) since
+    // the last rewrite of T. upk[m] packs u_0..u_3[m] and vpk[c] packs
+    // v_0..v_3[c] as signed bytes (exact: every |u|, |v| <= 127 for the
+    // instances this path is chosen for), so one dp4a adds all pending terms
+    // of an entry; bytes q >= np are masked off. T is rewritten once per four
+    // swaps. Exact integers throughout.
+    int np = 0;
+    if constexpr (PK > 1) {
+        for (int c = t; c < npad; c += G) {
+            upk[c] = 0u;
+            vpk[c] = 0u;
+        }
+    }
+
+    // T += sum_{q < np} u_q (x) v_q on this thread's (rows, column quads).
+    auto flush = [&]() {
+        const uint32_t mask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
+        int uw[ROWS];
+#pragma unroll
+        for (int k = 0; k < ROWS; ++k) {
+            const int m = lane + 32 * k;
+            uw[k] = m < n ? (int)(upk[m] & mask) : 0;
+        }
+        for (int cq = wg; cq < nq; cq += WPR) {
+            const int4 vq = reinterpret_cast<const int4 *>(vpk)[cq];
+#pragma unroll
+            for (int k = 0; k < ROWS; ++k) {
+                if (lane + 32 * k < n) {
+                    int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+                    int4 x = *row;
+                    x.x = __dp4a(uw[k], vq.x, x.x);
+                    x.y = __dp4a(uw[k], vq.y, x.y);
+                    x.z = __dp4a(uw[k], vq.z, x.z);
+                    x.w = __dp4a(uw[k], vq.w, x.w);
+                    *row = x;
+                }
+            }
+        }
+    };
 
     for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
         const float beta = a.mode == 1 ? beta_pt : a.beta[s];
@@ -305,6 +353,13 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 const int hi = sh[i];
                 const DT *Di = sD + i * n;
                 const DT *Fa = sF + fa * n;
+                // pending factors at this location: packed u_q[i] and v_q[fa]
+                const uint32_t pmask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
+                int ui4 = 0, vfa4 = 0;
+                if constexpr (PK > 1) {
+                    ui4 = (int)(upk[i] & pmask);
+                    vfa4 = (int)vpk[fa];
+                }
 
                 // ---- gather: Eq. 3 for every candidate j
                 int lmin = 0x7FFFFFFF;
@@ -315,7 +370,13 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         const int b = sp[j];
                         const int dij = Di[j];
                         const int fab = Fa[b];
-                        int d = 2 * (T[i * S + b] - hi + T[j * S + fa] - sh[j]);
+                        int row_ib = T[i * S + b];
+                        int col_ja = T[j * S + fa];
+                        if constexpr (PK > 1) {
+                            row_ib = __dp4a(ui4, (int)vpk[b], row_ib);
+                            col_ja = __dp4a((int)(upk[j] & pmask), vfa4, col_ja);
+                        }
+                        int d = 2 * (row_ib - hi + col_ja - sh[j]);
                         if (zero_diag)
                             d += 4 * dij * fab;
                         else
@@ -330,8 +391,10 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 if constexpr (WPR > 1) {
                     if (lane == 0) gs->wmin[wg] = dmin;
                     group_sync<WPR>(bar);
+                    int o = lane < WPR ? gs->wmin[lane] : 0x7FFFFFFF;
 #pragma unroll
-                    for (int w = 0; w < WPR; ++w) dmin = min(dmin, gs->wmin[w]);
+                    for (int w = 1; w < WPR; w <<= 1) o = min(o, __shfl_xor_sync(kFull, o, w));
+                    dmin = __shfl_sync(kFull, o, 0);
                 } else {
                     __syncwarp();
                 }
@@ -356,15 +419,16 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 if constexpr (WPR > 1) {
                     if (lane == 31) gs->wtot[wg] = incl;
                     group_sync<WPR>(bar);
-                    unsigned long long off = 0;
-                    total = 0;
+                    // lanes 0..WPR-1 hold the warp totals; inclusive scan over them
+                    unsigned long long wv = lane < WPR ? gs->wtot[lane] : 0ull;
 #pragma unroll
-                    for (int w = 0; w < WPR; ++w) {
-                        const unsigned long long v = gs->wtot[w];
-                        if (w < wg) off += v;
-                        total += v;
+                    for (int o = 1; o < WPR; o <<= 1) {
+                        const unsigned long long y = __shfl_up_sync(kFull, wv, o);
+                        if (lane >= o) wv += y;
                     }
-                    incl += off;
+                    total = __shfl_sync(kFull, wv, WPR - 1);
+                    const unsigned long long upto = __shfl_sync(kFull, wv, wg > 0 ? wg - 1 : 0);
+                    incl += wg > 0 ? upto : 0ull;
                 }
                 const unsigned long long excl = incl - lsum;
                 const unsigned long long tdraw = __umul64hi(draw, total);
@@ -382,13 +446,11 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 }
                 int js, dstar;
                 if constexpr (WPR > 1) {
-                    if (own) {
-                        gs->sel_j = jloc;
-                        gs->sel_d = dsel;
-                    }
+                    if (own) *reinterpret_cast<int2 *>(&gs->sel_j) = make_int2(jloc, dsel);
                     group_sync<WPR>(bar);
-                    js = gs->sel_j;
-                    dstar = gs->sel_d;
+                    const int2 sel = *reinterpret_cast<const int2 *>(&gs->sel_j);
+                    js = sel.x;
+                    dstar = sel.y;
                 } else {
                     const int src = __ffs(__ballot_sync(kFull, own)) - 1;
                     js = __shfl_sync(kFull, jloc, src);
@@ -397,78 +459,101 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 }
                 if (js == i) continue;
 
-                // ---- apply the swap i <-> js: rank-1 update of the table.
-                // Lane l of every warp owns rows l + 32 k; warp w of the group
-                // owns column quads w, w + WPR, ... so each warp reads each
-                // column-factor quad once.
+                // ---- apply the swap i <-> js
                 const int fb = sp[js];
                 const DT *Fb = sF + fb * n;
                 const DT *Dj = sD + js * n;
-                for (int c = t; c < npad; c += G) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
-                int u[ROWS];
-#pragma unroll
-                for (int k = 0; k < ROWS; ++k) {
-                    const int m = lane + 32 * k;
-                    u[k] = m < n ? (int)Di[m] - (int)Dj[m] : 0;
-                }
-                // old I[i][fb] and I[js][fa], for the two p-diagonal entries that move
+                // current I[i][fb] and I[js][fa], for the two p-diagonal entries that move
                 int tib = 0, tja = 0;
                 if (t == 0) {
                     tib = T[i * S + fb];
                     tja = T[js * S + fa];
-                }
-                group_sync<WPR>(bar);
-                const int4 *v4 = reinterpret_cast<const int4 *>(sv);
-                const int nq = npad / 4;
-                int cq = wg;
-                for (; cq + (QB - 1) * WPR < nq; cq += QB * WPR) {
-                    int4 vq[QB];
-#pragma unroll
-                    for (int b = 0; b < QB; ++b) vq[b] = v4[cq + b * WPR];
-                    int4 x[ROWS][QB];
-#pragma unroll
-                    for (int k = 0; k < ROWS; ++k) {
-                        if (lane + 32 * k < n) {
-                            const int4 *row = reinterpret_cast<const int4 *>(T + (lane + 32 * k) * S) + cq;
-#pragma unroll
-                            for (int b = 0; b < QB; ++b) x[k][b] = row[b * WPR];
-                        }
+                    if constexpr (PK > 1) {
+                        tib = __dp4a(ui4, (int)vpk[fb], tib);
+                        tja = __dp4a((int)(upk[js] & pmask), vfa4, tja);
                     }
+                }
+                if constexpr (PK == 1) {
+                    // Immediate rank-1 update: lane l of every warp owns rows
+                    // l + 32 k; warp w owns column quads w, w + WPR, ...
+                    for (int c = t; c < npad; c += G) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
+                    int u[ROWS];
 #pragma unroll
                     for (int k = 0; k < ROWS; ++k) {
-                        if (lane + 32 * k < n) {
-                            int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+                        const int m = lane + 32 * k;
+                        u[k] = m < n ? (int)Di[m] - (int)Dj[m] : 0;
+                    }
+                    group_sync<WPR>(bar);
+                    const int4 *v4 = reinterpret_cast<const int4 *>(sv);
+                    int cq = wg;
+                    for (; cq + (QB - 1) * WPR < nq; cq += QB * WPR) {
+                        int4 vq[QB];
 #pragma unroll
-                            for (int b = 0; b < QB; ++b) {
-                                add_scaled(x[k][b], u[k], vq[b]);
-                                row[b * WPR] = x[k][b];
+                        for (int b = 0; b < QB; ++b) vq[b] = v4[cq + b * WPR];
+                        int4 x[ROWS][QB];
+#pragma unroll
+                        for (int k = 0; k < ROWS; ++k) {
+                            if (lane + 32 * k < n) {
+                                const int4 *row = reinterpret_cast<const int4 *>(T + (lane + 32 * k) * S) + cq;
+#pragma unroll
+                                for (int b = 0; b < QB; ++b) x[k][b] = row[b * WPR];
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < ROWS; ++k) {
+                            if (lane + 32 * k < n) {
+                                int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+#pragma unroll
+                                for (int b = 0; b < QB; ++b) {
+                                    add_scaled(x[k][b], u[k], vq[b]);
+                                    row[b * WPR] = x[k][b];
+                                }
                             }
                         }
                     }
-                }
-                for (; cq < nq; cq += WPR) {
-                    const int4 vq = v4[cq];
+                    for (; cq < nq; cq += WPR) {
+                        const int4 vq = v4[cq];
 #pragma unroll
-                    for (int k = 0; k < ROWS; ++k) {
-                        if (lane + 32 * k < n) {
-                            int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
-                            int4 x = *row;
-                            add_scaled(x, u[k], vq);
-                            *row = x;
+                        for (int k = 0; k < ROWS; ++k) {
+                            if (lane + 32 * k < n) {
+                                int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+                                int4 x = *row;
+                                add_scaled(x, u[k], vq);
+                                *row = x;
+                            }
                         }
                     }
+                } else {
+                    // Deferred: record u and v of this swap in byte np of upk, vpk.
+                    int8_t *ub = reinterpret_cast<int8_t *>(upk) + np;
+                    int8_t *vb = reinterpret_cast<int8_t *>(vpk) + np;
+                    for (int c = t; c < npad; c += G) {
+                        ub[4 * c] = (int8_t)(c < n ? (int)Di[c] - (int)Dj[c] : 0);
+                        vb[4 * c] = (int8_t)(c < n ? (int)Fb[c] - (int)Fa[c] : 0);
+                    }
                 }
-                // p-diagonal h[m] = I[m][p(m)] under the new table and permutation:
-                // h[m] += u_m v[p(m)] where p(m) is unchanged; the two moved
-                // entries from the old I[i][fb], I[js][fa]. Thread 0 writes the
-                // new sp[i], sp[js]; those two are not read here.
+                // p-diagonal h[m] = I[m][p(m)] under the new influence and
+                // permutation: h[m] += u_m v[p(m)] where p(m) is unchanged;
+                // the two moved entries from the current I[i][fb], I[js][fa].
+                // Thread 0 writes sp[i], sp[js]; those two are not read here.
                 for (int m = t; m < n; m += G)
-                    if (m != i && m != js) sh[m] += ((int)Di[m] - (int)Dj[m]) * sv[sp[m]];
+                    if (m != i && m != js) {
+                        const int pm = sp[m];
+                        sh[m] += ((int)Di[m] - (int)Dj[m]) * ((int)Fb[pm] - (int)Fa[pm]);
+                    }
                 if (t == 0) {
                     sp[i] = fb;
                     sp[js] = fa;
-                    sh[i] = tib + ((int)Di[i] - (int)Dj[i]) * sv[fb];
-                    sh[js] = tja + ((int)Di[js] - (int)Dj[js]) * sv[fa];
+                    sh[i] = tib + ((int)Di[i] - (int)Dj[i]) * ((int)Fb[fb] - (int)Fa[fb]);
+                    sh[js] = tja + ((int)Di[js] - (int)Dj[js]) * ((int)Fb[fa] - (int)Fa[fa]);
+                }
+                if constexpr (PK > 1) {
+                    ++np;
+                    if (np == PK) {
+                        group_sync<WPR>(bar);  // packed factors and thread 0's table reads complete
+                        flush();
+                        np = 0;
+                    }
                 }
                 E += dstar;
                 acc_moves += 1;
@@ -479,6 +564,13 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 }
                 group_sync<WPR>(bar);
             }
+        }
+    }
+    if constexpr (PK > 1) {
+        if (np > 0) {
+            flush();
+            np = 0;
+            group_sync<WPR>(bar);
         }
     }
 
@@ -519,7 +611,7 @@ struct SweepBounds {
     static constexpr int threads = sweep_bound(MAXK, WPR);
 };
 
-template <typename DT, int MAXK, int WPR, bool TSMEM>
+template <typename DT, int MAXK, int WPR, bool TSMEM, int PK>
 __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int G = 32 * WPR;
@@ -542,16 +634,18 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(
     int32_t *sp = reinterpret_cast<int32_t *>(body + (TSMEM ? (size_t)n * a.stride * 4 : 0));
     int32_t *sh = sp + npad;
     int32_t *sv = sh + npad;
+    uint32_t *upk = reinterpret_cast<uint32_t *>(sv + a.sv_len);  // [npad], PK > 1 only
+    uint32_t *vpk = upk + npad;
     for (;;) {
         if (t == 0) gs->item = atomicAdd(a.queue, 1);
         group_sync<WPR>(bar);
         const int item = gs->item;
         if (item >= a.replicas) break;
         if constexpr (TSMEM) {
-            run_replica<DT, MAXK, WPR>(a, item, t, bar, sD, sF, sT, sp, sh, sv, gs);
+            run_replica<DT, MAXK, WPR, PK>(a, item, t, bar, sD, sF, sT, sp, sh, sv, upk, vpk, gs);
         } else {
-            run_replica<DT, MAXK, WPR>(a, item, t, bar, sD, sF, a.tables + (size_t)item * n * a.stride,
-                                       sp, sh, sv, gs);
+            run_replica<DT, MAXK, WPR, PK>(a, item, t, bar, sD, sF,
+                                           a.tables + (size_t)item * n * a.stride, sp, sh, sv, upk, vpk, gs);
         }
     }
 }
@@ -560,23 +654,27 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(
 // pdit_sweep_i8.cu, pdit_sweep_i16.cu, pdit_sweep_i32.cu). Return a
 // cudaError_t value; cudaErrorInvalidValue for a shape with no kernel.
 template <typename DT>
-int sweep_blocks_per_sm(int maxk, int wpr, bool tsmem, int threads, size_t smem, int *blocks);
+int sweep_blocks_per_sm(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, int *blocks);
 template <typename DT>
-int sweep_launch(int maxk, int wpr, bool tsmem, const SweepArgs &a, int grid, int threads, size_t smem,
-                 cudaStream_t stream);
+int sweep_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid, int threads,
+                 size_t smem, cudaStream_t stream);
 
 // Shapes with a compiled kernel: (MAXK, WPR) with 32 * WPR * MAXK in
-// {32, 64, 128, 256}; the global-table variant only for 256.
-#define PDIT_SWEEP_SHAPES(X)                                                                     \
-    X(1, 1, true) X(2, 1, true) X(1, 2, true) X(4, 1, true) X(2, 2, true) X(1, 4, true)          \
-    X(8, 1, true) X(4, 2, true) X(2, 4, true) X(1, 8, true)                                      \
-    X(8, 1, false) X(4, 2, false) X(2, 4, false) X(1, 8, false)
+// {32, 64, 128, 256}; the global-table variant only for 256; deferred
+// updates (PK = 4) only with tables in shared memory.
+#define PDIT_SWEEP_SHAPES_COMMON(X)                                                              \
+    X(1, 1, true, 1) X(2, 1, true, 1) X(1, 2, true, 1) X(4, 1, true, 1) X(2, 2, true, 1)         \
+    X(1, 4, true, 1) X(8, 1, true, 1) X(4, 2, true, 1) X(2, 4, true, 1) X(1, 8, true, 1)         \
+    X(8, 1, false, 1) X(4, 2, false, 1) X(2, 4, false, 1) X(1, 8, false, 1)
+#define PDIT_SWEEP_SHAPES_DEFERRED(X)                                                            \
+    X(1, 1, true, 4) X(2, 1, true, 4) X(1, 2, true, 4) X(4, 1, true, 4) X(2, 2, true, 4)         \
+    X(1, 4, true, 4) X(8, 1, true, 4) X(4, 2, true, 4) X(2, 4, true, 4) X(1, 8, true, 4)
 
-#define PDIT_INSTANTIATE_SWEEP(DT)                                                               \
-    template <int MAXK, int WPR, bool TSMEM>                                                     \
+#define PDIT_INSTANTIATE_SWEEP(DT, SHAPES)                                                       \
+    template <int MAXK, int WPR, bool TSMEM, int PK>                                             \
     static int sweep_one(const SweepArgs &a, int grid, int threads, size_t smem,                \
                          cudaStream_t st, int *blocks, bool query) {                             \
-        auto fn = sweep_kernel<DT, MAXK, WPR, TSMEM>;                                            \
+        auto fn = sweep_kernel<DT, MAXK, WPR, TSMEM, PK>;                                        \
         if (threads > SweepBounds<MAXK, WPR>::threads) return (int)cudaErrorInvalidValue;        \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                              (int)smem);                                         \
@@ -586,26 +684,29 @@ int sweep_launch(int maxk, int wpr, bool tsmem, const SweepArgs &a, int grid, in
         fn<<<grid, threads, smem, st>>>(a);                                                      \
         return (int)cudaGetLastError();                                                          \
     }                                                                                            \
-    static int sweep_dispatch(int maxk, int wpr, bool tsmem, const SweepArgs &a, int grid,       \
-                              int threads, size_t smem, cudaStream_t st, int *blocks,            \
+    static int sweep_dispatch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a,         \
+                              int grid, int threads, size_t smem, cudaStream_t st, int *blocks,  \
                               bool query) {                                                      \
-        PDIT_SWEEP_SHAPES(PDIT_CASE)                                                             \
+        SHAPES(PDIT_CASE)                                                                        \
         return (int)cudaErrorInvalidValue;                                                       \
     }                                                                                            \
     template <>                                                                                  \
-    int sweep_blocks_per_sm<DT>(int maxk, int wpr, bool tsmem, int threads, size_t smem,         \
+    int sweep_blocks_per_sm<DT>(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, \
                                 int *blocks) {                                                   \
         SweepArgs dummy{};                                                                       \
-        return sweep_dispatch(maxk, wpr, tsmem, dummy, 0, threads, smem, nullptr, blocks, true); \
+        return sweep_dispatch(maxk, wpr, tsmem, pk, dummy, 0, threads, smem, nullptr, blocks,    \
+                              true);                                                             \
     }                                                                                            \
     template <>                                                                                  \
-    int sweep_launch<DT>(int maxk, int wpr, bool tsmem, const SweepArgs &a, int grid,            \
+    int sweep_launch<DT>(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid,    \
                          int threads, size_t smem, cudaStream_t st) {                            \
-        return sweep_dispatch(maxk, wpr, tsmem, a, grid, threads, smem, st, nullptr, false);     \
+        return sweep_dispatch(maxk, wpr, tsmem, pk, a, grid, threads, smem, st, nullptr, false); \
     }
 
-#define PDIT_CASE(MK, W, TS)                                                                     \
-    if (maxk == MK && wpr == W && tsmem == TS)                                                   \
-        return sweep_one<MK, W, TS>(a, grid, threads, smem, st, blocks, query);
+#define PDIT_CASE(MK, W, TS, K)                                                                  \
+    if (maxk == MK && wpr == W && tsmem == TS && pk == K)                                        \
+        return sweep_one<MK, W, TS, K>(a, grid, threads, smem, st, blocks, query);
+
+#define PDIT_SWEEP_SHAPES_ALL(X) PDIT_SWEEP_SHAPES_COMMON(X) PDIT_SWEEP_SHAPES_DEFERRED(X)
 
 }  // namespace pdit

@@ -107,6 +107,8 @@ def lib():
     L.pdit_set_warps_per_replica.restype = ctypes.c_int
     L.pdit_launch_shape.argtypes = [vp, ctypes.c_int, vp]
     L.pdit_launch_shape.restype = ctypes.c_int
+    L.pdit_set_pending_swaps.argtypes = [vp, ctypes.c_int]
+    L.pdit_set_pending_swaps.restype = ctypes.c_int
     L.pdit_strerror.argtypes = [ctypes.c_int]
     L.pdit_strerror.restype = ctypes.c_char_p
     L.pdit_last_error.argtypes = []
@@ -206,11 +208,15 @@ def pdit_set_warps_per_replica(q: Qap, wpr: int):
     _check(lib().pdit_set_warps_per_replica(q.handle, wpr), "pdit_set_warps_per_replica")
 
 
+def pdit_set_pending_swaps(q: Qap, k: int):
+    _check(lib().pdit_set_pending_swaps(q.handle, k), "pdit_set_pending_swaps")
+
+
 def pdit_launch_shape(q: Qap, replicas: int) -> dict:
-    out = np.zeros(6, dtype=np.int32)
+    out = np.zeros(7, dtype=np.int32)
     _check(lib().pdit_launch_shape(q.handle, replicas, _ptr(out)), "pdit_launch_shape")
     return dict(zip(["warps_per_replica", "candidates_per_thread", "replicas_per_cta", "ctas",
-                     "tables_in_smem", "smem_bytes"], (int(x) for x in out)))
+                     "tables_in_smem", "smem_bytes", "pending_swaps"], (int(x) for x in out)))
 
 
 def pdit_beta_max(q: Qap) -> float:

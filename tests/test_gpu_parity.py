@@ -30,11 +30,13 @@ def P():
     return pdit
 
 
-def gpu_run(D, F, beta, sweeps, seed, R, tables=False, wpr=0, **kw):
+def gpu_run(D, F, beta, sweeps, seed, R, tables=False, wpr=0, pk=0, **kw):
     p = P()
     with p.Qap(D, F) as q:
         if wpr:
             p.pdit_set_warps_per_replica(q, wpr)
+        if pk:
+            p.pdit_set_pending_swaps(q, pk)
         dbeta = torch.from_numpy(np.ascontiguousarray(beta, np.float32)).cuda() if len(beta) else \
             torch.zeros(1, dtype=torch.float32, device="cuda")
         out = p.anneal_device(q, R, dbeta, sweeps, seed, per_replica=True, tables=tables, **kw)
@@ -123,16 +125,31 @@ def test_sizes_dense(n):
     check_equal(g, r, tables=True)
 
 
-@pytest.mark.parametrize("n,wpr", [(30, 1), (40, 1), (40, 2), (100, 1), (100, 2), (100, 4), (129, 1),
-                                   (129, 2), (129, 4), (129, 8), (190, 8), (256, 1), (256, 2), (256, 4),
-                                   (256, 8)])
-def test_every_thread_mapping(n, wpr):
-    """Every warps-per-replica shape gives the oracle's results."""
+MAPPINGS = [(30, 1, 1), (30, 1, 4), (40, 1, 1), (40, 2, 1), (40, 1, 4), (40, 2, 4), (100, 1, 1),
+            (100, 2, 1), (100, 4, 1), (100, 1, 4), (100, 2, 4), (100, 4, 4), (129, 1, 1), (129, 2, 4),
+            (129, 4, 1), (129, 8, 4), (190, 8, 1), (190, 4, 4), (256, 1, 1), (256, 2, 1), (256, 4, 1),
+            (256, 8, 1)]
+
+
+@pytest.mark.parametrize("n,wpr,pk", MAPPINGS)
+def test_every_thread_mapping(n, wpr, pk):
+    """Every warps-per-replica shape, with immediate (1) or deferred (4)
+    table updates, gives the oracle's results."""
     D, F = G.dense_instance(n, seed=n + 7)
     sweeps = 5
     beta = schedule(D, F, "linear", sweeps) * np.float32(0.5)
-    g = gpu_run(D, F, beta, sweeps, 21, 4, tables=True, wpr=wpr)
+    g = gpu_run(D, F, beta, sweeps, 21, 4, tables=True, wpr=wpr, pk=pk)
     r = O.anneal(D, F, beta, sweeps, 21, 0, 4, threads=4, tables=True)
+    check_equal(g, r, tables=True)
+
+
+def test_deferred_updates_long_run_with_flush_boundaries():
+    """Deferred updates over many accepted swaps, sweeps ending mid-batch,
+    resumed calls: still bit-exact."""
+    D, F = G.named("n30")
+    beta = schedule(D, F, "linear", 37)
+    g = gpu_run(D, F, beta, 37, 5, 10, tables=True, pk=4)
+    r = O.anneal(D, F, beta, 37, 5, 0, 10, threads=5, tables=True)
     check_equal(g, r, tables=True)
 
 
