@@ -387,14 +387,13 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         lmin = min(lmin, d);
                     }
                 }
-                int dmin = warp_min(lmin);
+                int dmin = __reduce_min_sync(kFull, lmin);
                 if constexpr (WPR > 1) {
                     if (lane == 0) gs->wmin[wg] = dmin;
                     group_sync<WPR>(bar);
-                    int o = lane < WPR ? gs->wmin[lane] : 0x7FFFFFFF;
+                    dmin = gs->wmin[0];
 #pragma unroll
-                    for (int w = 1; w < WPR; w <<= 1) o = min(o, __shfl_xor_sync(kFull, o, w));
-                    dmin = __shfl_sync(kFull, o, 0);
+                    for (int w = 1; w < WPR; ++w) dmin = min(dmin, gs->wmin[w]);
                 } else {
                     __syncwarp();
                 }
@@ -419,16 +418,17 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 if constexpr (WPR > 1) {
                     if (lane == 31) gs->wtot[wg] = incl;
                     group_sync<WPR>(bar);
-                    // lanes 0..WPR-1 hold the warp totals; inclusive scan over them
-                    unsigned long long wv = lane < WPR ? gs->wtot[lane] : 0ull;
+                    // every thread reads all warp totals (broadcast) and sums the
+                    // ones before its warp
+                    unsigned long long off = 0;
+                    total = 0;
 #pragma unroll
-                    for (int o = 1; o < WPR; o <<= 1) {
-                        const unsigned long long y = __shfl_up_sync(kFull, wv, o);
-                        if (lane >= o) wv += y;
+                    for (int w = 0; w < WPR; ++w) {
+                        const unsigned long long v = gs->wtot[w];
+                        off += w < wg ? v : 0ull;
+                        total += v;
                     }
-                    total = __shfl_sync(kFull, wv, WPR - 1);
-                    const unsigned long long upto = __shfl_sync(kFull, wv, wg > 0 ? wg - 1 : 0);
-                    incl += wg > 0 ? upto : 0ull;
+                    incl += off;
                 }
                 const unsigned long long excl = incl - lsum;
                 const unsigned long long tdraw = __umul64hi(draw, total);
