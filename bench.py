@@ -65,15 +65,25 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float) -> float:
+def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pending: int = 1) -> float:
     """Shared-memory bytes one update must move in this design.
-    Gather (every update): p[j], I[i][p(j)], I[j][p(i)], h[j] as int32, plus
-    D[i][j] and F[p(i)][p(j)] at the staged width: 16 N + 2 N dt.
-    Accepted swap: read+write of the N x N int32 table (8 N^2), the two F
-    rows and two D rows (4 N dt), the column factor written once (4 N) and
-    the p-diagonal gathered and rewritten (8 N)."""
-    gather = 16 * n + 2 * n * dt_bytes
-    swap = 8 * n * n + 4 * n * dt_bytes + 12 * n
+    Immediate table updates (pending = 1):
+      gather, every update: p[j], I[i][p(j)], I[j][p(i)], h[j] as int32, plus
+      D[i][j] and F[p(i)][p(j)] at the staged width dt: 16 N + 2 N dt;
+      accepted swap: read+write of the N x N int32 table (8 N^2), two D rows
+      and two F rows (4 N dt), the column factor written once (4 N), the
+      p-diagonal read and written (8 N).
+    Deferred updates (pending = 4): the gather also reads the packed factors
+    u[j], v[p(j)] (+8 N); an accepted swap writes one byte of each packed
+    factor per entry (2 N), reads two D rows and two F rows (4 N dt) and p,
+    h (12 N), and a quarter of a table rewrite with its packed factors
+    (2 N^2 + 2 N)."""
+    if pending <= 1:
+        gather = 16 * n + 2 * n * dt_bytes
+        swap = 8 * n * n + 4 * n * dt_bytes + 12 * n
+    else:
+        gather = 24 * n + 2 * n * dt_bytes
+        swap = 2 * n * n + 4 * n * dt_bytes + 16 * n
     return gather + accept_frac * swap
 
 
@@ -323,7 +333,7 @@ def main():
     # roofline of the sweep kernel: shared-memory bound
     props = torch.cuda.get_device_properties(dev)
     dt_bytes = 1 if max(abs(int(D.max())), abs(int(F.max()))) <= 127 else 2
-    bpu = algorithmic_bytes_per_update(n, dt_bytes, accept_frac)
+    bpu = algorithmic_bytes_per_update(n, dt_bytes, accept_frac, shape["pending_swaps"])
     kernel_s = tot_ms / 1000.0 / args.steps
     achieved = bpu * upd_rank / kernel_s / 1e9
     sm_mhz = clk.get("sm_mhz") or 0.0
