@@ -206,6 +206,39 @@ int pdit_beta_max(const pdit_qap *h, double *beta_max);
  */
 int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out);
 
+/*
+ * pdit_anneal_noalloc -- the annealed p-dit sweep of pdit_anneal_ex for
+ * callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is not allowed or not wanted (inside a framework that owns every
+ * device allocation through its own pool, or in a process that must not grow
+ * its device footprint after start-up). It makes no cudaMalloc, cudaFree or
+ * other allocating call. The paper has no counterpart; this is a packaging
+ * of the same computation.
+ *   n, D, F  : instance size and DEVICE pointers to the int32 row-major
+ *              matrices, symmetric, 16 (n+2) max|D| max|F| < 2^31 (not
+ *              checked here: the values stay on the device).
+ *   replicas, beta (DEVICE, `sweeps` floats), sweeps, seed: as pdit_anneal.
+ *   best_perm (DEVICE, n int32), best_cost (DEVICE, 1 int64): outputs.
+ *   stream   : cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Replica ids are 0..replicas-1, instance id 0: the results equal those of
+ * pdit_anneal / pdit_anneal_ex with the same arguments.
+ * The per-replica state lives in one static device array of
+ * PDIT_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps until
+ * exit. A call needs about replicas * (8 n + 36) bytes of it; larger calls
+ * return PDIT_ENOMEM. The staged matrices must fit shared memory with one
+ * replica table (n <= 150 or so): PDIT_ENOTSUP otherwise.
+ * Every call shares the array and it keeps the last call's contents: calls
+ * that overlap on the GPU (different streams, or host threads) race on it;
+ * serialise them. The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.
+ * Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ENOTSUP, PDIT_ECUDA.
+ */
+#define PDIT_NOALLOC_SCRATCH_BYTES (8u << 20)
+int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas, const float *beta,
+                        int sweeps, uint64_t seed, int32_t *best_perm, int64_t *best_cost,
+                        void *stream);
+
 /* pdit_strerror -- static text for an error code. */
 const char *pdit_strerror(int code);
 

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -625,6 +626,119 @@ int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out) {
         const double b = kind == 0 ? beta_max * f : (beta_max / 1000.0) * std::pow(1000.0, f);
         out[s] = (float)b;
     }
+    return PDIT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point. Its scratch (the per-replica state that
+// pdit_anneal_ex keeps in a workspace) is this file-scope device array, so
+// the call never allocates device memory. In host code `g_noalloc_scratch`
+// names a host-side stand-in, not a device address: the address is taken
+// with cudaGetSymbolAddress once per device, with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[PDIT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(int device, void **out) {
+    if (device < 0 || device >= kMaxDevices) return PDIT_ENOTSUP;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return PDIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas, const float *beta,
+                        int sweeps, uint64_t seed, int32_t *best_perm, int64_t *best_cost,
+                        void *stream) {
+    if (n < 2 || n > PDIT_N_MAX || !D || !F || replicas < 1 || sweeps < 0) return PDIT_EINVAL;
+    if (!best_perm || !best_cost || (sweeps > 0 && !beta)) return PDIT_EINVAL;
+    if ((uint64_t)sweeps >= 0xFFFFFFFFull) return PDIT_EINVAL;
+    // A stand-in instance description on the stack: D and F are read as
+    // int32 with the general (any diagonal) swap energy and immediate table
+    // updates, since their values are not inspected on the host here.
+    pdit_qap q;
+    q.n = n;
+    q.dt_bytes = 4;
+    q.zero_diag = 0;
+    q.packed_ok = 0;
+    q.dD = const_cast<int32_t *>(D);
+    q.dF = const_cast<int32_t *>(F);
+    int v = 0;
+    PDIT_CK(cudaGetDevice(&q.device));
+    PDIT_CK(cudaDeviceGetAttribute(&q.num_sms, cudaDevAttrMultiProcessorCount, q.device));
+    PDIT_CK(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, q.device));
+    q.smem_optin = (size_t)v;
+    pdit_opts o;
+    pdit_opts_init(&o);
+    o.replicas = replicas;
+    o.sweeps = sweeps;
+    o.seed = seed;
+    o.beta = beta;
+    o.stream = stream;
+    o.best_perm = best_perm;
+    o.best_cost = best_cost;
+    Plan plan;
+    int rc = make_plan(&q, replicas, 0, 1, &plan);
+    q.dD = q.dF = nullptr;  // not owned: nothing for ~pdit_qap to release
+    if (rc) return rc;
+    if (!plan.tsmem) return PDIT_ENOTSUP;
+    const Workspace need = carve(&q, &o, plan, nullptr);
+    if (need.bytes > (size_t)PDIT_NOALLOC_SCRATCH_BYTES) return PDIT_ENOMEM;
+    void *scratch = nullptr;
+    rc = noalloc_scratch(q.device, &scratch);
+    if (rc) return rc;
+    const Workspace w = carve(&q, &o, plan, (char *)scratch);
+    cudaStream_t st = (cudaStream_t)stream;
+    // The array keeps the previous call's contents: reset the status word
+    // and the work counter; every replica's state is rewritten from scratch.
+    PDIT_CK(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+    PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
+    pdit::SweepArgs a{};
+    a.D = D;
+    a.F = F;
+    a.n = n;
+    a.stride = plan.stride;
+    a.zero_diag = 0;
+    a.replicas = replicas;
+    a.sweep_begin = 0;
+    a.sweep_end = sweeps;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.beta = beta;
+    a.fresh = 1;
+    a.perm = w.perm;
+    a.best_perm = w.best_perm;
+    a.energy = w.energy;
+    a.best_energy = w.best_energy;
+    a.best_sweep = w.best_sweep;
+    a.accepted = w.accepted;
+    a.rung = w.rung;
+    a.queue = w.queue;
+    a.status = w.status;
+    a.df_bytes = plan.df_bytes;
+    a.group_bytes = plan.group_bytes;
+    a.sv_len = plan.sv_len;
+    const int e = sweep_launch(4, plan, a, st);
+    if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
+    finalize_kernel<<<1, 1024, 0, st>>>(replicas, n, w.best_energy, w.best_perm, best_perm, best_cost,
+                                        w.status, nullptr);
+    PDIT_CK(cudaGetLastError());
     return PDIT_OK;
 }
 

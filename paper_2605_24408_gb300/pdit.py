@@ -109,6 +109,9 @@ def lib():
     L.pdit_launch_shape.restype = ctypes.c_int
     L.pdit_set_pending_swaps.argtypes = [vp, ctypes.c_int]
     L.pdit_set_pending_swaps.restype = ctypes.c_int
+    L.pdit_anneal_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_uint64,
+                                      vp, vp, vp]
+    L.pdit_anneal_noalloc.restype = ctypes.c_int
     L.pdit_strerror.argtypes = [ctypes.c_int]
     L.pdit_strerror.restype = ctypes.c_char_p
     L.pdit_last_error.argtypes = []
@@ -230,6 +233,15 @@ def pdit_beta_schedule(kind: str, sweeps: int, beta_max: float) -> np.ndarray:
     _check(lib().pdit_beta_schedule({"linear": 0, "geometric": 1}[kind], sweeps, beta_max, _ptr(out)),
            "pdit_beta_schedule")
     return out[:sweeps]
+
+
+def pdit_anneal_noalloc(n: int, D_ptr: int, F_ptr: int, replicas: int, beta_ptr: int, sweeps: int,
+                        seed: int, best_perm_ptr: int, best_cost_ptr: int, stream_ptr: int = 0) -> int:
+    """The allocation-free entry point on raw device pointers; returns the code."""
+    return lib().pdit_anneal_noalloc(n, ctypes.c_void_p(D_ptr), ctypes.c_void_p(F_ptr), replicas,
+                                     ctypes.c_void_p(beta_ptr), sweeps, seed & 0xFFFFFFFFFFFFFFFF,
+                                     ctypes.c_void_p(best_perm_ptr), ctypes.c_void_p(best_cost_ptr),
+                                     ctypes.c_void_p(stream_ptr))
 
 
 def opts(**kw) -> pdit_opts:
