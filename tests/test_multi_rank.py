@@ -1,0 +1,76 @@
+"""The multi-GPU split of the replica space, on CPU ranks (gloo, world size 2).
+
+Each rank runs its shard of replicas (global ids r*R .. r*R+R-1) and the
+ranks agree on the best cost with the lowest global replica id and that
+replica's permutation. The per-rank work is done by the CPU oracle here (no
+GPU on this host); what is tested is the host-side split and exchange of
+paper_2605_24408_gb300.multi, against one process running every replica."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import oracle as O
+from paper_2605_24408_gb300 import instances as G
+
+
+def _free_port() -> int:
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, R, sweeps, seed, out_q):
+    import torch.distributed as dist
+
+    from paper_2605_24408_gb300 import multi
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        D, F = G.named("n12")
+        beta = O.beta_schedule("linear", sweeps, O.beta_max(D, F))
+        base, cnt = multi.shard(rank, world, R)
+        r = O.anneal(D, F, beta, sweeps, seed, base, base + cnt)
+        cost, gid, perm = multi.global_best(r["cost"], r["winner"], r["perm"], base)
+        out_q.put((rank, cost, gid, perm.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2])
+def test_sharded_replicas_agree_with_one_process(world):
+    R, sweeps, seed = 6, 30, 4
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, R, sweeps, seed, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    D, F = G.named("n12")
+    beta = O.beta_schedule("linear", sweeps, O.beta_max(D, F))
+    full = O.anneal(D, F, beta, sweeps, seed, 0, world * R)
+    for _, cost, gid, perm in results:
+        assert cost == full["cost"]
+        assert gid == full["winner"]
+        assert np.array_equal(np.array(perm, np.int32), full["perm"])
+
+
+def test_shard_ranges_cover_the_replica_space():
+    from paper_2605_24408_gb300 import multi
+
+    seen = []
+    for r in range(4):
+        base, cnt = multi.shard(r, 4, 10)
+        seen.extend(range(base, base + cnt))
+    assert seen == list(range(40))
