@@ -51,6 +51,7 @@ extern "C" {
 /* Modes. */
 #define PDIT_MODE_ANNEAL 0 /* beta[s] for sweep s, every replica */
 #define PDIT_MODE_PT 1     /* parallel tempering over a beta ladder */
+#define PDIT_MODE_FIXED 2  /* beta[r] for replica r, every sweep, no exchange (beta-range trials) */
 
 /* Flags. */
 #define PDIT_FLAG_RESUME 1u /* continue from the replica state already in the workspace */
@@ -143,8 +144,8 @@ typedef struct pdit_opts {
     uint64_t seed;          /* Philox key */
     uint32_t instance_id;   /* Philox counter word 0; default 0 */
     uint32_t replica_base;  /* global id of this call's replica 0 (counter word 1); default 0 */
-    int mode;               /* PDIT_MODE_ANNEAL (default) or PDIT_MODE_PT */
-    const float *beta;      /* anneal: [sweeps]; PT: [ladder_len], rung 0 = smallest beta */
+    int mode;               /* PDIT_MODE_ANNEAL (default), PDIT_MODE_PT or PDIT_MODE_FIXED */
+    const float *beta;      /* anneal: [sweeps]; PT: [ladder_len], rung 0 = smallest beta; fixed: [replicas] */
     int ladder_len;         /* PT: replicas per set (2..64); replicas % ladder_len == 0 */
     int exchange_period;    /* PT: sweeps between exchanges (paper: 4) */
     int timeout_periods;    /* PT: periods without a top-rung swap before top<->bottom (paper: 100); 0 = off */
@@ -238,6 +239,36 @@ int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out);
 int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas, const float *beta,
                         int sweeps, uint64_t seed, int32_t *best_perm, int64_t *best_cost,
                         void *stream);
+
+/*
+ * pdit_beta_range -- the paper's beta-range selection (Implementation
+ * section; CPU-PIM Algorithm section; Fig. 2b): short trials at fixed beta
+ * without any exchange, whose ending energies (not best energies) are
+ * averaged per beta.
+ *   points              : >= 3 beta values, geometric from beta_min to beta_max
+ *                         (both > 0; otherwise beta_max_conv/1000 .. 10 beta_max_conv
+ *                         with beta_max_conv from pdit_beta_max).
+ *   replicas_per_point  : trial replicas per beta value (ids point*rpp + k).
+ *   sweeps              : trial length (the paper uses 400 iterations).
+ *   seed                : Philox key of the trials.
+ *   beta_lo, beta_hi    : outputs: beta_lo = the first (smallest) beta whose
+ *                         mean ending energy has come down to within 40% of
+ *                         the largest-minus-smallest mean above the smallest
+ *                         mean; beta_hi = the beta two grid points past the one
+ *                         with the smallest mean (clamped to the grid).
+ *   curve               : optional host [points]: the mean ending energies.
+ * Synchronous; allocates and frees temporary device buffers.
+ * Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ECUDA.
+ */
+int pdit_beta_range(pdit_qap *h, int points, double beta_min, double beta_max, int replicas_per_point,
+                    int sweeps, uint64_t seed, double *beta_lo, double *beta_hi, double *curve);
+
+/*
+ * pdit_beta_ladder -- fill out[len] with beta_lo (beta_hi/beta_lo)^(q/(len-1)),
+ * the multiplicative ladder of the parallel-tempering replicas (CPU-PIM
+ * Algorithm section: 10 replicas per set). Errors: PDIT_EINVAL.
+ */
+int pdit_beta_ladder(double beta_lo, double beta_hi, int len, float *out);
 
 /* pdit_strerror -- static text for an error code. */
 const char *pdit_strerror(int code);

@@ -197,7 +197,8 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
            period: int = 4, timeout: int = 100, near: bool = False, tables: bool = False) -> dict:
     """Runs replicas [rep_begin, rep_end). mode 'anneal': beta[s] per sweep;
     mode 'pt': beta is the ladder (rung 0 = smallest beta), sets of ladder_len
-    consecutive replicas exchange every `period` sweeps."""
+    consecutive replicas exchange every `period` sweeps; mode 'fixed':
+    beta[k] for the k-th replica of the call, no exchange."""
     D, F = _i32(D), _i32(F)
     n = D.shape[0]
     R = rep_end - rep_begin
@@ -209,7 +210,7 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
     tab = np.zeros((R, n, n), np.int64) if tables else None
     rung = np.zeros(R, np.int32) if mode == "pt" else None
     rc = lib().oracle_anneal(
-        n, D, F, rep_begin, rep_end, 1 if mode == "pt" else 0, ladder_len, period, timeout,
+        n, D, F, rep_begin, rep_end, {"anneal": 0, "pt": 1, "fixed": 2}[mode], ladder_len, period, timeout,
         beta, sweeps, seed, inst, threads, out["final_perm"], out["final_cost"],
         out["best_perm"], out["best_cost"], out["best_sweep"], out["accepted"],
         nb.ctypes.data if nb is not None else None,
@@ -228,3 +229,38 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
     out["cost"] = int(out["best_cost"][w])
     out["perm"] = out["best_perm"][w].copy()
     return out
+
+
+# --- beta-range selection (Implementation section, CPU-PIM Algorithm, Fig. 2b) ---
+
+def beta_grid(points: int, bmin: float, bmax: float) -> np.ndarray:
+    """Geometric grid of `points` betas from bmin to bmax (double, then binary32)."""
+    return np.array([np.float32(bmin * (bmax / bmin) ** (k / (points - 1))) for k in range(points)],
+                    dtype=np.float32)
+
+
+def select_beta_range(mean_energy) -> tuple[int, int]:
+    """Indices (lo, hi) from the mean ending energy per beta (ascending beta):
+    lo = first point at or below min + 0.4 (max - min); hi = two points past
+    the minimum, clamped to the grid."""
+    e = np.asarray(mean_energy, dtype=np.float64)
+    kmin = int(np.argmin(e))
+    thr = e[kmin] + 0.4 * (e.max() - e[kmin])
+    lo = int(np.flatnonzero(e <= thr)[0])
+    hi = min(kmin + 2, len(e) - 1)
+    return lo, hi
+
+
+def beta_range(D, F, points: int = 32, bmin: float = 0.0, bmax: float = 0.0, rpp: int = 8,
+               sweeps: int = 400, seed: int = 0, threads: int = 8):
+    """Short fixed-beta trials without exchange; returns (beta_lo, beta_hi,
+    mean ending energy per point, grid)."""
+    if not (bmin > 0 and bmax > bmin):
+        b = beta_max(D, F)
+        bmin, bmax = b / 1000.0, b * 10.0
+    grid = beta_grid(points, bmin, bmax)
+    rbeta = np.repeat(grid, rpp).astype(np.float32)
+    r = anneal(D, F, rbeta, sweeps, seed, 0, points * rpp, threads=threads, mode="fixed")
+    mean = r["final_cost"].reshape(points, rpp).astype(np.float64).mean(axis=1)
+    lo, hi = select_beta_range(mean)
+    return float(grid[lo]), float(grid[hi]), mean, grid

@@ -24,7 +24,8 @@
  *                         valid permutation, each sweep every p-dit
  *                         initiates one update (order R3); incremental
  *                         influence update after each swap (Methods,
- *                         GPU-CUPIM Algorithm: "incrementally updated I");
+ *                         GPU-CUPIM Algorithm: the sequential PIM keeps I
+ *                         up to date incrementally);
  *                         best-so-far as first logged (Hardware and Data
  *                         Reporting Details, reading R6); parallel
  *                         tempering (Implementation + CPU-PIM Algorithm,
@@ -96,8 +97,8 @@ uint64_t oracle_update_draw(uint64_t seed, uint32_t inst, uint32_t rep, uint32_t
     return (uint64_t)out[0] | ((uint64_t)out[1] << 32);
 }
 
-/* Reading R5: uniform random initial permutation ("each p-dit is initialized
- * with a unique dimension", Implementation section). Fisher-Yates from the
+/* Reading R5: uniform random initial permutation (every p-dit starts in a
+ * distinct dimension, Implementation section). Fisher-Yates from the
  * last position down; the index for step k is the high word of u * (k + 1). */
 void oracle_init_perm(int n, uint64_t seed, uint32_t inst, uint32_t rep, int32_t *p) {
     uint32_t key[2];
@@ -346,7 +347,7 @@ typedef struct {
     int n;
     const int32_t *D, *F;
     int rep_begin, rep_end;   /* replicas [rep_begin, rep_end) */
-    int mode;                 /* 0: anneal with beta[sweep]; 1: PT with beta[rung] */
+    int mode;                 /* 0: anneal with beta[sweep]; 1: PT with beta[rung]; 2: beta[replica] */
     int ladder_len, period, timeout;
     const float *beta;        /* anneal: [sweeps]; PT: [ladder_len] */
     int sweeps;
@@ -394,7 +395,7 @@ static void run_job(anneal_job_t *J) {
         for (int k = 0; k < R; ++k) {
             replica_t *X = &reps[k];
             uint32_t rep = (uint32_t)(J->rep_begin + k);
-            float beta = J->mode == 1 ? J->beta[rung[k]] : J->beta[s];
+            float beta = J->mode == 1 ? J->beta[rung[k]] : J->mode == 2 ? J->beta[k] : J->beta[s];
             for (int i = 0; i < n; ++i) {
                 uint64_t r = oracle_update_draw(J->seed, J->inst, rep, (uint32_t)s, (uint32_t)i);
                 int64_t *dE = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -479,7 +480,7 @@ int oracle_anneal(int n, const int32_t *D, const int32_t *F, int rep_begin, int 
         J->ladder_len = ladder_len;
         J->period = period;
         J->timeout = timeout;
-        J->beta = beta;
+        J->beta = mode == 2 ? beta + k0 : beta;
         J->sweeps = sweeps;
         J->seed = seed;
         J->inst = inst;

@@ -287,7 +287,7 @@ int validate_opts(const pdit_qap *h, const pdit_opts *o) {
     if ((uint64_t)o->sweeps >= 0xFFFFFFFFull) return PDIT_EINVAL;
     if (!o->best_perm || !o->best_cost) return PDIT_EINVAL;
     if (se > o->sweep_begin && !o->beta) return PDIT_EINVAL;
-    if (o->mode != PDIT_MODE_ANNEAL && o->mode != PDIT_MODE_PT) return PDIT_EINVAL;
+    if (o->mode != PDIT_MODE_ANNEAL && o->mode != PDIT_MODE_PT && o->mode != PDIT_MODE_FIXED) return PDIT_EINVAL;
     if (o->mode == PDIT_MODE_PT) {
         if (o->ladder_len < 2 || o->ladder_len > 64 || o->replicas % o->ladder_len) return PDIT_EINVAL;
         if (o->exchange_period < 1 || o->timeout_periods < 0) return PDIT_EINVAL;
@@ -480,7 +480,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.key1 = (uint32_t)(o->seed >> 32);
     a.inst = o->instance_id;
     a.rep_base = o->replica_base;
-    a.mode = pt ? 1 : 0;
+    a.mode = o->mode;
     a.beta = o->beta;
     a.perm = w.perm;
     a.best_perm = w.best_perm;
@@ -615,6 +615,94 @@ int pdit_beta_max(const pdit_qap *h, double *beta_max) {
             }
         }
     *beta_max = cnt ? 10.0 / (sum / (double)cnt) : 1.0;
+    return PDIT_OK;
+}
+
+int pdit_beta_ladder(double beta_lo, double beta_hi, int len, float *out) {
+    if (len < 1 || !out || !(beta_lo > 0.0) || !(beta_hi >= beta_lo) || !std::isfinite(beta_hi))
+        return PDIT_EINVAL;
+    for (int q = 0; q < len; ++q) {
+        const double f = len > 1 ? (double)q / (double)(len - 1) : 0.0;
+        out[q] = (float)(beta_lo * std::pow(beta_hi / beta_lo, f));
+    }
+    return PDIT_OK;
+}
+
+int pdit_beta_range(pdit_qap *h, int points, double beta_min, double beta_max, int replicas_per_point,
+                    int sweeps, uint64_t seed, double *beta_lo, double *beta_hi, double *curve) {
+    if (!h || points < 3 || replicas_per_point < 1 || sweeps < 1 || !beta_lo || !beta_hi) return PDIT_EINVAL;
+    if ((int64_t)points * replicas_per_point > (1 << 24)) return PDIT_EINVAL;
+    if (!(beta_min > 0.0) || !(beta_max > beta_min) || !std::isfinite(beta_max)) {
+        double b = 0.0;
+        const int rc = pdit_beta_max(h, &b);
+        if (rc) return rc;
+        beta_min = b / 1000.0;
+        beta_max = b * 10.0;
+    }
+    std::vector<float> grid((size_t)points);
+    for (int k = 0; k < points; ++k)
+        grid[k] = (float)(beta_min * std::pow(beta_max / beta_min, (double)k / (double)(points - 1)));
+    const int R = points * replicas_per_point;
+    std::vector<float> rbeta((size_t)R);
+    for (int r = 0; r < R; ++r) rbeta[r] = grid[r / replicas_per_point];
+    if (!h->stream) PDIT_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    // Temporary device buffers: betas, final costs, best permutation, best cost.
+    float *dbeta = nullptr;
+    int64_t *dfinal = nullptr, *dcost = nullptr;
+    int32_t *dperm = nullptr;
+    cudaError_t e = cudaMalloc((void **)&dbeta, sizeof(float) * R);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dfinal, sizeof(int64_t) * R);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dcost, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dperm, sizeof(int32_t) * h->n);
+    std::vector<int64_t> fin((size_t)R);
+    int rc = PDIT_OK;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dbeta, rbeta.data(), sizeof(float) * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        pdit_opts o;
+        pdit_opts_init(&o);
+        o.replicas = R;
+        o.sweeps = sweeps;
+        o.seed = seed;
+        o.mode = PDIT_MODE_FIXED;
+        o.beta = dbeta;
+        o.stream = h->stream;
+        o.best_perm = dperm;
+        o.best_cost = dcost;
+        o.replica_final_cost = dfinal;
+        rc = pdit_anneal_ex(h, &o);
+        if (!rc) e = cudaMemcpyAsync(fin.data(), dfinal, sizeof(int64_t) * R, cudaMemcpyDeviceToHost, h->stream);
+        if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    cudaFree(dbeta);
+    cudaFree(dfinal);
+    cudaFree(dcost);
+    cudaFree(dperm);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "pdit_beta_range");
+    // Mean ending energy per beta; lowest beta: the first point whose mean has
+    // come down to 40% of the way from the smallest to the largest mean;
+    // highest beta: two points past the smallest mean (clamped to the grid).
+    std::vector<double> mean((size_t)points, 0.0);
+    for (int r = 0; r < R; ++r) mean[r / replicas_per_point] += (double)fin[r];
+    for (int k = 0; k < points; ++k) mean[k] /= (double)replicas_per_point;
+    int kmin = 0, kmax = 0;
+    for (int k = 1; k < points; ++k) {
+        if (mean[k] < mean[kmin]) kmin = k;
+        if (mean[k] > mean[kmax]) kmax = k;
+    }
+    const double thr = mean[kmin] + 0.4 * (mean[kmax] - mean[kmin]);
+    int klo = kmin;
+    for (int k = 0; k < points; ++k)
+        if (mean[k] <= thr) {
+            klo = k;
+            break;
+        }
+    const int khi = std::min(kmin + 2, points - 1);
+    *beta_lo = (double)grid[klo];
+    *beta_hi = (double)grid[khi];
+    if (curve)
+        for (int k = 0; k < points; ++k) curve[k] = mean[k];
     return PDIT_OK;
 }
 

@@ -42,7 +42,7 @@ struct SweepArgs {
     uint32_t key0, key1;   // Philox key = seed
     uint32_t inst;         // Philox counter word 0
     uint32_t rep_base;     // global id of local replica 0 (counter word 1)
-    int mode;              // 0 anneal (beta[s]), 1 parallel tempering (beta[rung])
+    int mode;              // 0 anneal (beta[s]), 1 parallel tempering (beta[rung]), 2 fixed (beta[r])
     const float *beta;
     int fresh;             // start from a Fisher-Yates permutation
     int table_in;          // take the influence table from `tables` instead of rebuilding it
@@ -291,7 +291,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     }
     group_sync<WPR>(bar);
 
-    const float beta_pt = (a.mode == 1 && a.sweep_end > a.sweep_begin) ? a.beta[a.rung[r]] : 0.0f;
+    const float beta_fixed = a.sweep_end <= a.sweep_begin ? 0.0f
+                           : a.mode == 1 ? a.beta[a.rung[r]] : a.mode == 2 ? a.beta[r] : 0.0f;
     const int zero_diag = a.zero_diag;
     const int nq = npad / 4;
 
@@ -339,7 +340,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     };
 
     for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
-        const float beta = a.mode == 1 ? beta_pt : a.beta[s];
+        const float beta = a.mode != 0 ? beta_fixed : a.beta[s];
         for (int i0 = 0; i0 < n; i0 += 32) {
             // Philox(inst, replica, sweep, location) for the next 32 locations.
             const uint4 rw = philox4x32_10(a.inst, grep, (uint32_t)s, (uint32_t)(i0 + lane), a.key0, a.key1);

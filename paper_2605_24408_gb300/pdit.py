@@ -28,6 +28,7 @@ PDIT_ENOTSUP = -6
 PDIT_N_MAX = 256
 PDIT_MODE_ANNEAL = 0
 PDIT_MODE_PT = 1
+PDIT_MODE_FIXED = 2
 PDIT_FLAG_RESUME = 1
 
 _lib = None
@@ -109,6 +110,11 @@ def lib():
     L.pdit_launch_shape.restype = ctypes.c_int
     L.pdit_set_pending_swaps.argtypes = [vp, ctypes.c_int]
     L.pdit_set_pending_swaps.restype = ctypes.c_int
+    L.pdit_beta_range.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_uint64, vp, vp, vp]
+    L.pdit_beta_range.restype = ctypes.c_int
+    L.pdit_beta_ladder.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    L.pdit_beta_ladder.restype = ctypes.c_int
     L.pdit_anneal_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_uint64,
                                       vp, vp, vp]
     L.pdit_anneal_noalloc.restype = ctypes.c_int
@@ -226,6 +232,23 @@ def pdit_beta_max(q: Qap) -> float:
     out = ctypes.c_double()
     _check(lib().pdit_beta_max(q.handle, ctypes.byref(out)), "pdit_beta_max")
     return float(out.value)
+
+
+def pdit_beta_range(q: Qap, points: int = 32, beta_min: float = 0.0, beta_max: float = 0.0,
+                    replicas_per_point: int = 8, sweeps: int = 400, seed: int = 0):
+    """Returns (beta_lo, beta_hi, mean ending energy per grid point)."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    curve = np.zeros(points, dtype=np.float64)
+    _check(lib().pdit_beta_range(q.handle, points, beta_min, beta_max, replicas_per_point, sweeps,
+                                 seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(lo), ctypes.byref(hi), _ptr(curve)),
+           "pdit_beta_range")
+    return float(lo.value), float(hi.value), curve
+
+
+def pdit_beta_ladder(beta_lo: float, beta_hi: float, length: int = 10) -> np.ndarray:
+    out = np.zeros(length, dtype=np.float32)
+    _check(lib().pdit_beta_ladder(beta_lo, beta_hi, length, _ptr(out)), "pdit_beta_ladder")
+    return out
 
 
 def pdit_beta_schedule(kind: str, sweeps: int, beta_max: float) -> np.ndarray:

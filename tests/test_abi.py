@@ -74,3 +74,13 @@ def test_workspace_and_anneal_reject_null_handle(L):
     assert L.pdit_anneal_ex(None, ctypes.byref(o)) == P.PDIT_EINVAL
     assert L.pdit_anneal(None, 4, None, 0, 0, None, None) == P.PDIT_EINVAL
     assert L.qap_n(None) == P.PDIT_EINVAL
+
+
+def test_beta_ladder_is_multiplicative(L):
+    lad = P.pdit_beta_ladder(0.01, 1.0, 10)
+    want = np.float32([0.01 * (100.0 ** (q / 9)) for q in range(10)])
+    assert np.array_equal(lad, want)
+    with pytest.raises(P.PditError):
+        P.pdit_beta_ladder(0.0, 1.0, 10)
+    with pytest.raises(P.PditError):
+        P.pdit_beta_ladder(1.0, 0.5, 10)

@@ -273,3 +273,25 @@ def test_parallel_tempering_matches_oracle(n, timeout):
     r = O.anneal(D, F, ladder, S, 5, 0, R, mode="pt", ladder_len=L, period=4, timeout=timeout, threads=4)
     check_equal(g, r)
     assert np.array_equal(g["replica_rung"], r["rung"])
+
+
+# --- fixed beta per replica and the beta-range selection ------------------------
+
+def test_fixed_beta_mode_matches_oracle():
+    D, F = G.named("n30")
+    bm = O.beta_max(D, F)
+    betas = np.float32([bm * f for f in (0.0, 0.01, 0.1, 0.5, 1.0, 3.0, 10.0, 30.0)])
+    g = gpu_run(D, F, betas, 40, 12, 8, mode=2)
+    r = O.anneal(D, F, betas, 40, 12, 0, 8, mode="fixed", threads=8)
+    check_equal(g, r)
+
+
+def test_beta_range_selection_matches_oracle():
+    D, F = G.named("n30")
+    p = P()
+    with p.Qap(D, F) as q:
+        lo, hi, curve = p.pdit_beta_range(q, points=16, replicas_per_point=4, sweeps=100, seed=5)
+    olo, ohi, omean, grid = O.beta_range(D, F, points=16, rpp=4, sweeps=100, seed=5)
+    assert np.array_equal(curve, omean)
+    assert lo == olo and hi == ohi
+    assert lo <= hi

@@ -391,3 +391,35 @@ def test_beta_schedules():
         if d > 0:
             pos.append(d)
     assert O.beta_max(D, F) == pytest.approx(10.0 / np.mean(pos), rel=1e-12)
+
+
+# --- Beta-range selection ------------------------------------------------------
+
+def test_select_beta_range_hand_cases():
+    # min 5, max 100: threshold 5 + 0.4 * 95 = 43 -> first point at or below is index 3;
+    # the minimum is at index 5 -> two points past it is index 7.
+    assert O.select_beta_range([100, 90, 60, 30, 10, 5, 7, 9]) == (3, 7)
+    # minimum at the end of the grid: clamp.
+    assert O.select_beta_range([50, 50, 49, 48, 47, 40, 41]) == (5, 6)
+    # frozen uptick after the minimum (the shape the paper describes)
+    assert O.select_beta_range([9.0, 8.0, 3.0, 1.0, 2.0, 4.0, 6.0]) == (2, 5)
+
+
+def test_fixed_beta_mode_equals_constant_schedules():
+    """Mode 'fixed' (beta per replica) is the plain anneal of each replica with
+    a constant schedule at its beta."""
+    D, F = G.named("n12")
+    betas = np.float32([0.0, 0.05, 0.3, 2.0])
+    r = O.anneal(D, F, betas, 25, 9, 0, 4, mode="fixed")
+    for k, b in enumerate(betas):
+        single = O.anneal(D, F, np.full(25, b, np.float32), 25, 9, k, k + 1)
+        assert np.array_equal(r["final_perm"][k], single["final_perm"][0])
+        assert r["best_cost"][k] == single["best_cost"][0]
+
+
+def test_beta_range_curve_shape_on_n12():
+    D, F = G.named("n12")
+    lo, hi, mean, grid = O.beta_range(D, F, points=12, rpp=4, sweeps=60, seed=3, threads=4)
+    assert grid[0] <= lo <= hi <= grid[-1]
+    # high temperature: mean ending energy well above the brute-force optimum
+    assert mean[0] > 564 and mean.min() >= 564
