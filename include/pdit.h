@@ -109,8 +109,8 @@ int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape);
  * swaps as pending rank-1 terms that every query adds in, and rewrites the
  * table once per four swaps (a rank-4 update). 0 restores the built-in
  * choice. k = 4 needs max - min <= 127 over the entries of D and of F (so
- * every swap factor fits a signed byte) and the tables in shared memory
- * (PDIT_ENOTSUP otherwise, at the next call). Results do not depend on k.
+ * every swap factor fits a signed byte) (PDIT_ENOTSUP otherwise, at the next
+ * call). Results do not depend on k.
  * Errors: PDIT_EINVAL.
  */
 int pdit_set_pending_swaps(pdit_qap *h, int k);
@@ -165,6 +165,15 @@ typedef struct pdit_opts {
     int32_t *replica_rung;       /* [replicas]: PT rung of each replica at the end */
     int32_t *tables;             /* [replicas * n * n]: final influence tables I[m][c] */
     int32_t *status;             /* [1]: PDIT_STATUS_* bits, 0 if every audit passed */
+    /* time to a target cost (optional) */
+    const int64_t *target;       /* [1]: the cost to reach */
+    uint64_t *reach_ns;          /* [1]: %globaltimer (ns) when some replica's best first got
+                                    <= *target; UINT64_MAX if never */
+    int32_t *reach_sweep;        /* [1]: the smallest sweep index at which a replica's best was
+                                    <= *target (-1 = its initial state); INT32_MAX if never */
+    int stop_at_target;          /* 1: once reached, every replica stops at its next sweep
+                                    (results then depend on timing; reach_* stay exact only
+                                    without stopping) */
 } pdit_opts;
 
 /* pdit_opts_init -- defaults (see the field comments). NULL-safe. */
@@ -269,6 +278,56 @@ int pdit_beta_range(pdit_qap *h, int points, double beta_min, double beta_max, i
  * Algorithm section: 10 replicas per set). Errors: PDIT_EINVAL.
  */
 int pdit_beta_ladder(double beta_lo, double beta_hi, int len, float *out);
+
+/*
+ * Multi-instance batch: many instances of different sizes annealed by one
+ * persistent launch per compiled kernel shape (instances of the same shape
+ * share a launch; shapes run concurrently), all enqueued by one call and, on
+ * request, captured once into a CUDA graph and replayed. Each instance's
+ * results equal those of pdit_anneal_ex with the same arguments.
+ */
+typedef struct pdit_batch pdit_batch;
+
+typedef struct pdit_batch_item {
+    pdit_qap *qap;           /* the instance (not owned; must outlive the batch) */
+    int replicas;            /* >= 1, replica ids 0..replicas-1 */
+    int sweeps;              /* >= 0 */
+    const float *beta;       /* DEVICE [sweeps] */
+    uint64_t seed;
+    uint32_t instance_id;    /* Philox counter word 0 */
+    int32_t *best_perm;      /* DEVICE [n] output */
+    int64_t *best_cost;      /* DEVICE [1] output */
+    const int64_t *target;   /* DEVICE [1] or NULL: as pdit_opts.target */
+    uint64_t *reach_ns;      /* DEVICE [1] or NULL */
+    int32_t *reach_sweep;    /* DEVICE [1] or NULL */
+} pdit_batch_item;
+
+#define PDIT_BATCH_STOP_AT_TARGET 1u /* replicas of an instance stop once its target is reached */
+#define PDIT_BATCH_GRAPH 2u          /* capture the launch sequence into a CUDA graph on the first run */
+
+/*
+ * pdit_batch_create -- plan a batch: per instance the launch shape of
+ * pdit_launch_shape (its handle's settings apply), instances grouped by
+ * shape, work units of one CTA's worth of replicas ordered by decreasing
+ * cost, one device workspace. `items` is copied. Allocates device memory
+ * and streams. Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ENOTSUP, PDIT_ECUDA.
+ */
+int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, pdit_batch **out);
+
+/*
+ * pdit_batch_run -- anneal every instance of the batch, asynchronously on
+ * `stream` (cudaStream_t, NULL = legacy default stream). With
+ * PDIT_BATCH_GRAPH the first call captures the sequence on `stream` (which
+ * must not be the legacy default stream) and every call launches the graph.
+ * Errors: PDIT_EINVAL, PDIT_ECUDA.
+ */
+int pdit_batch_run(pdit_batch *b, void *stream);
+
+/* pdit_batch_info -- number of shape classes (launches) and workspace bytes. */
+int pdit_batch_info(const pdit_batch *b, int *classes, size_t *workspace_bytes);
+
+/* pdit_batch_destroy -- free the batch (not the instances). NULL-safe. */
+void pdit_batch_destroy(pdit_batch *b);
 
 /* pdit_strerror -- static text for an error code. */
 const char *pdit_strerror(int code);

@@ -74,7 +74,8 @@ def lib():
         L.oracle_pt_exchange.restype = None
         L.oracle_anneal.argtypes = [c_int, I32P, I32P, c_int, c_int, c_int, c_int, c_int, c_int,
                                     F32P, c_int, c_u64, c_u32, c_int,
-                                    I32P, I64P, I32P, I64P, I32P, I64P, vp, vp, vp]
+                                    I32P, I64P, I32P, I64P, I32P, I64P, vp, vp, vp,
+                                    c_int, c_i64, vp]
         L.oracle_anneal.restype = c_int
         L.oracle_argmin_best.argtypes = [c_int, I64P]
         L.oracle_argmin_best.restype = c_int
@@ -194,7 +195,8 @@ def beta_schedule(kind: str, sweeps: int, bmax: float) -> np.ndarray:
 
 def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int = 1,
            inst: int = 0, threads: int = 1, mode: str = "anneal", ladder_len: int = 0,
-           period: int = 4, timeout: int = 100, near: bool = False, tables: bool = False) -> dict:
+           period: int = 4, timeout: int = 100, near: bool = False, tables: bool = False,
+           target=None) -> dict:
     """Runs replicas [rep_begin, rep_end). mode 'anneal': beta[s] per sweep;
     mode 'pt': beta is the ladder (rung 0 = smallest beta), sets of ladder_len
     consecutive replicas exchange every `period` sweeps; mode 'fixed':
@@ -209,13 +211,16 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
     nb = np.zeros(R, np.int64) if near else None
     tab = np.zeros((R, n, n), np.int64) if tables else None
     rung = np.zeros(R, np.int32) if mode == "pt" else None
+    reach = np.zeros(R, np.int32) if target is not None else None
     rc = lib().oracle_anneal(
         n, D, F, rep_begin, rep_end, {"anneal": 0, "pt": 1, "fixed": 2}[mode], ladder_len, period, timeout,
         beta, sweeps, seed, inst, threads, out["final_perm"], out["final_cost"],
         out["best_perm"], out["best_cost"], out["best_sweep"], out["accepted"],
         nb.ctypes.data if nb is not None else None,
         tab.ctypes.data if tab is not None else None,
-        rung.ctypes.data if rung is not None else None)
+        rung.ctypes.data if rung is not None else None,
+        1 if target is not None else 0, int(target) if target is not None else 0,
+        reach.ctypes.data if reach is not None else None)
     if rc != 0:
         raise ValueError("oracle_anneal rejected its arguments")
     if nb is not None:
@@ -224,6 +229,8 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
         out["tables"] = tab
     if rung is not None:
         out["rung"] = rung
+    if reach is not None:
+        out["reach_sweep"] = reach
     w = int(lib().oracle_argmin_best(R, out["best_cost"]))
     out["winner"] = w
     out["cost"] = int(out["best_cost"][w])

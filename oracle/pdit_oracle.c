@@ -363,6 +363,9 @@ typedef struct {
     int64_t *near;        /* [R] or NULL */
     int64_t *final_I;     /* [R*n*n] or NULL */
     int32_t *final_rung;  /* [R] or NULL (PT) */
+    int has_target;       /* record the first sweep at which best <= target */
+    int64_t target;
+    int32_t *reach;       /* [R] or NULL: that sweep (-1 = initial state), INT32_MAX if never */
     int status;
 } anneal_job_t;
 
@@ -388,6 +391,7 @@ static void run_job(anneal_job_t *J) {
         J->best_E[k] = X->E;
         J->best_sweep[k] = -1;
         J->accepted[k] = 0;
+        if (J->reach) J->reach[k] = (J->has_target && X->E <= J->target) ? -1 : 0x7FFFFFFF;
         if (J->near) J->near[k] = 0;
         if (J->mode == 1) rung[k] = (int32_t)(rep % (uint32_t)J->ladder_len);
     }
@@ -409,6 +413,9 @@ static void run_job(anneal_job_t *J) {
                         J->best_E[k] = X->E;
                         J->best_sweep[k] = s;
                         memcpy(J->best_p + (size_t)k * n, X->p, sizeof(int32_t) * (size_t)n);
+                        if (J->reach && J->has_target && J->reach[k] == 0x7FFFFFFF &&
+                            X->E <= J->target)
+                            J->reach[k] = s;
                     }
                 }
                 free(dE);
@@ -452,7 +459,8 @@ int oracle_anneal(int n, const int32_t *D, const int32_t *F, int rep_begin, int 
                   int mode, int ladder_len, int period, int timeout, const float *beta,
                   int sweeps, uint64_t seed, uint32_t inst, int threads, int32_t *final_p,
                   int64_t *final_E, int32_t *best_p, int64_t *best_E, int32_t *best_sweep,
-                  int64_t *accepted, int64_t *near, int64_t *final_I, int32_t *final_rung) {
+                  int64_t *accepted, int64_t *near, int64_t *final_I, int32_t *final_rung,
+                  int has_target, int64_t target, int32_t *reach) {
     if (n < 2 || rep_end <= rep_begin || sweeps < 0 || !D || !F || !beta) return -1;
     int R = rep_end - rep_begin;
     int unit = 1;
@@ -493,6 +501,9 @@ int oracle_anneal(int n, const int32_t *D, const int32_t *F, int rep_begin, int 
         J->near = near ? near + k0 : NULL;
         J->final_I = final_I ? final_I + (size_t)k0 * n * n : NULL;
         J->final_rung = final_rung ? final_rung + k0 : NULL;
+        J->has_target = has_target;
+        J->target = target;
+        J->reach = reach ? reach + k0 : NULL;
     }
     if (threads == 1) {
         run_job(&jobs[0]);

@@ -106,24 +106,24 @@ size_t group_bytes_for(int n, int stride, int cover, bool tsmem, int pk) {
 
 // Launch shape for `replicas` chains of an n-location instance. `wpr` = warps
 // per replica (0: choose).
-int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p) {
+int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t reserve = 0) {
     const int n = h->n;
     const int cover = cover_for(n);
     p->stride = table_stride(n);
     p->sv_len = sv_len_for(p->stride, cover);
     p->df_bytes = align_up((size_t)2 * n * n * h->dt_bytes, 16);
-    const size_t budget = h->smem_optin;
+    const size_t budget = h->smem_optin - reserve;
     p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1) <= budget;
     if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;
-    const bool defer_ok = p->tsmem && h->packed_ok;
+    const bool defer_ok = h->packed_ok != 0;
     if (pk != 0 && pk != 1 && pk != 4) return PDIT_EINVAL;
     if (pk == 4 && !defer_ok) return PDIT_ENOTSUP;
     if (pk == 0) {
         // Defer table rewrites when the ring costs no replica slot.
         pk = 1;
         if (defer_ok) {
-            const size_t g1 = group_bytes_for(n, p->stride, cover, true, 1);
-            const size_t g4 = group_bytes_for(n, p->stride, cover, true, 4);
+            const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1);
+            const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4);
             if ((budget - p->df_bytes) / g4 == (budget - p->df_bytes) / g1) pk = 4;
         }
     }
@@ -157,7 +157,7 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p) {
 }
 
 struct Workspace {
-    int32_t *perm, *best_perm, *best_sweep, *rung, *since_top, *queue, *status, *tables;
+    int32_t *perm, *best_perm, *best_sweep, *rung, *since_top, *queue, *status, *tables, *done;
     int64_t *energy, *best_energy, *accepted;
     size_t bytes;
 };
@@ -184,6 +184,7 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.since_top = (int32_t *)take(4 * nsets);
     w.queue = (int32_t *)take(4 * 64);
     w.status = (int32_t *)take(4);
+    w.done = (int32_t *)take(4);
     w.tables = needs_tables(o, p) ? (int32_t *)take(4 * R * n * (size_t)p.stride) : nullptr;
     w.bytes = off;
     return w;
@@ -192,6 +193,15 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
 // ---------------------------------------------------------------------------
 // Device helpers: PT rung initialisation and exchange, final reduction.
 // ---------------------------------------------------------------------------
+// Reset the time-to-target outputs of one instance.
+__global__ void init_target_kernel(unsigned long long *reach_ns, int *reach_sweep, int *done) {
+    if (threadIdx.x == 0) {
+        if (reach_ns) *reach_ns = ~0ull;
+        if (reach_sweep) *reach_sweep = 0x7FFFFFFF;
+        if (done) *done = 0;
+    }
+}
+
 __global__ void init_pt_kernel(int replicas, int ladder, int32_t *rung, int32_t *since_top,
                                uint32_t rep_base) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,6 +472,10 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
 
     if (!resume) {
         PDIT_CK(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+        if (o->target) {
+            init_target_kernel<<<1, 32, 0, st>>>((unsigned long long *)o->reach_ns, o->reach_sweep, w.done);
+            PDIT_CK(cudaGetLastError());
+        }
         if (pt) {
             init_pt_kernel<<<(R + 255) / 256, 256, 0, st>>>(R, o->ladder_len, w.rung, w.since_top,
                                                             o->replica_base);
@@ -495,6 +509,12 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.df_bytes = plan.df_bytes;
     a.group_bytes = plan.group_bytes;
     a.sv_len = plan.sv_len;
+    a.groups = plan.groups;
+    a.target = o->target;
+    a.reach_ns = (unsigned long long *)o->reach_ns;
+    a.reach_sweep = o->reach_sweep;
+    a.done = o->target ? w.done : nullptr;
+    a.stop = (o->target && o->stop_at_target) ? 1 : 0;
 
     // Segments: the whole range in anneal mode; exchange periods in PT mode.
     bool first = true;
@@ -827,6 +847,359 @@ int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas,
     finalize_kernel<<<1, 1024, 0, st>>>(replicas, n, w.best_energy, w.best_perm, best_perm, best_cost,
                                         w.status, nullptr);
     PDIT_CK(cudaGetLastError());
+    return PDIT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Multi-instance batches.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kBatchStaticSmem = 512;
+
+struct BatchOut {
+    int32_t *perm;
+    int64_t *cost;
+    int n, replicas;
+    const int64_t *best_energy;
+    const int32_t *best_perm;
+};
+
+struct BatchClass {
+    int dt = 1, maxk = 1, wpr = 1, pk = 1;
+    bool tsmem = true;
+    int threads = 32, grid = 1, nunits = 0;
+    size_t smem = 0;
+    std::vector<int> items;
+    pdit::BatchUnit *d_units = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+int batch_blocks(int dt, const BatchClass &c, int *blocks) {
+    if (dt == 1) return pdit::batch_blocks_per_sm<int8_t>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
+    if (dt == 2) return pdit::batch_blocks_per_sm<int16_t>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
+    return pdit::batch_blocks_per_sm<int32_t>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
+}
+
+int batch_launch(const BatchClass &c, const pdit::SweepArgs *descs, int *queue) {
+    if (c.dt == 1)
+        return pdit::batch_launch<int8_t>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
+                                          c.grid, c.threads, c.smem, c.stream);
+    if (c.dt == 2)
+        return pdit::batch_launch<int16_t>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
+                                           c.grid, c.threads, c.smem, c.stream);
+    return pdit::batch_launch<int32_t>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
+                                       c.grid, c.threads, c.smem, c.stream);
+}
+
+// Per instance: reset its time-to-target outputs and stop flag.
+__global__ void batch_init_kernel(int count, const pdit::SweepArgs *descs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const pdit::SweepArgs &a = descs[k];
+    if (a.reach_ns) *a.reach_ns = ~0ull;
+    if (a.reach_sweep) *a.reach_sweep = 0x7FFFFFFF;
+    if (a.done) *a.done = 0;
+}
+
+// One block per instance: smallest best energy over its replicas (ties to the
+// lowest replica) and that replica's permutation.
+__global__ void batch_finalize_kernel(const BatchOut *outs) {
+    const BatchOut o = outs[blockIdx.x];
+    __shared__ long long sval[32];
+    __shared__ int sidx[32];
+    __shared__ int winner;
+    long long v = 0x7FFFFFFFFFFFFFFFll;
+    int idx = 0x7FFFFFFF;
+    for (int r = threadIdx.x; r < o.replicas; r += blockDim.x) {
+        const long long e = o.best_energy[r];
+        if (e < v || (e == v && r < idx)) {
+            v = e;
+            idx = r;
+        }
+    }
+    for (int off = 16; off; off >>= 1) {
+        const long long ov = __shfl_xor_sync(0xFFFFFFFFu, v, off);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, idx, off);
+        if (ov < v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sval[warp] = v;
+        sidx[warp] = idx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long bv = sval[0];
+        int bi = sidx[0];
+        for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w)
+            if (sval[w] < bv || (sval[w] == bv && sidx[w] < bi)) {
+                bv = sval[w];
+                bi = sidx[w];
+            }
+        winner = bi;
+        *o.cost = bv;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < o.n; m += blockDim.x) o.perm[m] = o.best_perm[(size_t)winner * o.n + m];
+}
+
+}  // namespace
+
+struct pdit_batch {
+    int device = 0;
+    uint32_t flags = 0;
+    std::vector<pdit_batch_item> items;
+    std::vector<BatchClass> classes;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    pdit::SweepArgs *d_descs = nullptr;
+    BatchOut *d_outs = nullptr;
+    int *d_queues = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int batch_enqueue(pdit_batch *b, cudaStream_t st) {
+    const int count = (int)b->items.size();
+    PDIT_CK(cudaMemsetAsync(b->d_queues, 0, sizeof(int) * b->classes.size(), st));
+    batch_init_kernel<<<(count + 127) / 128, 128, 0, st>>>(count, b->d_descs);
+    PDIT_CK(cudaGetLastError());
+    PDIT_CK(cudaEventRecord(b->fork, st));
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        BatchClass &k = b->classes[c];
+        PDIT_CK(cudaStreamWaitEvent(k.stream, b->fork, 0));
+        const int e = batch_launch(k, b->d_descs, b->d_queues + c);
+        if (e != 0) return cuda_fail((cudaError_t)e, "batch kernel launch");
+        PDIT_CK(cudaEventRecord(k.done, k.stream));
+        PDIT_CK(cudaStreamWaitEvent(st, k.done, 0));
+    }
+    batch_finalize_kernel<<<count, 256, 0, st>>>(b->d_outs);
+    PDIT_CK(cudaGetLastError());
+    return PDIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pdit_batch_destroy(pdit_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (BatchClass &c : b->classes) {
+        cudaFree(c.d_units);
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    cudaFree(b->ws);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_outs);
+    cudaFree(b->d_queues);
+    delete b;
+}
+
+int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, pdit_batch **out) {
+    if (!out) return PDIT_EINVAL;
+    *out = nullptr;
+    if (!items || count < 1 || (flags & ~(PDIT_BATCH_STOP_AT_TARGET | PDIT_BATCH_GRAPH))) return PDIT_EINVAL;
+    int dev = 0;
+    PDIT_CK(cudaGetDevice(&dev));
+    for (int k = 0; k < count; ++k) {
+        const pdit_batch_item &it = items[k];
+        if (!it.qap || it.replicas < 1 || it.sweeps < 0 || (it.sweeps > 0 && !it.beta)) return PDIT_EINVAL;
+        if (!it.best_perm || !it.best_cost || it.qap->device != dev) return PDIT_EINVAL;
+        if ((uint64_t)it.sweeps >= 0xFFFFFFFFull) return PDIT_EINVAL;
+    }
+    pdit_batch *b = new (std::nothrow) pdit_batch();
+    if (!b) return PDIT_ENOMEM;
+    b->device = dev;
+    b->flags = flags;
+    b->items.assign(items, items + count);
+    // Per instance: its shape with as many replica groups per CTA as fit.
+    std::vector<Plan> plans((size_t)count);
+    std::vector<size_t> ws_off((size_t)count);
+    size_t ws_total = 0;
+    for (int k = 0; k < count; ++k) {
+        pdit_qap *h = items[k].qap;
+        // the multi-instance kernel keeps its instance descriptor in static shared memory
+        int rc = make_plan(h, 1 << 28, h->force_wpr, h->force_pk, &plans[k], kBatchStaticSmem);
+        if (rc) {
+            delete b;
+            return rc;
+        }
+        pdit_opts o;
+        pdit_opts_init(&o);
+        o.replicas = items[k].replicas;
+        ws_off[k] = ws_total;
+        ws_total += align_up(carve(h, &o, plans[k], nullptr).bytes, kAlign);
+    }
+    // Shape classes.
+    for (int k = 0; k < count; ++k) {
+        const Plan &p = plans[k];
+        const int dt = items[k].qap->dt_bytes;
+        int found = -1;
+        for (size_t c = 0; c < b->classes.size(); ++c) {
+            const BatchClass &x = b->classes[c];
+            if (x.dt == dt && x.maxk == p.maxk && x.wpr == p.wpr && x.pk == p.pk && x.tsmem == p.tsmem) found = (int)c;
+        }
+        if (found < 0) {
+            BatchClass x;
+            x.dt = dt;
+            x.maxk = p.maxk;
+            x.wpr = p.wpr;
+            x.pk = p.pk;
+            x.tsmem = p.tsmem;
+            b->classes.push_back(x);
+            found = (int)b->classes.size() - 1;
+        }
+        BatchClass &x = b->classes[found];
+        x.items.push_back(k);
+        x.threads = std::max(x.threads, p.threads);
+        x.smem = std::max(x.smem, p.smem);
+    }
+    int rc = PDIT_OK;
+    cudaError_t e = cudaMalloc(&b->ws, std::max<size_t>(ws_total, 256));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_descs, sizeof(pdit::SweepArgs) * count);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_outs, sizeof(BatchOut) * count);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_queues, sizeof(int) * b->classes.size());
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        rc = e == cudaErrorMemoryAllocation ? PDIT_ENOMEM : cuda_fail(e, "pdit_batch_create");
+        pdit_batch_destroy(b);
+        return rc;
+    }
+    b->ws_bytes = ws_total;
+    // Descriptors.
+    std::vector<pdit::SweepArgs> descs((size_t)count);
+    std::vector<BatchOut> outs((size_t)count);
+    for (int k = 0; k < count; ++k) {
+        const pdit_batch_item &it = items[k];
+        const Plan &p = plans[k];
+        pdit_qap *h = it.qap;
+        pdit_opts o;
+        pdit_opts_init(&o);
+        o.replicas = it.replicas;
+        const Workspace w = carve(h, &o, p, (char *)b->ws + ws_off[k]);
+        pdit::SweepArgs &a = descs[k];
+        a = pdit::SweepArgs{};
+        a.D = h->dD;
+        a.F = h->dF;
+        a.n = h->n;
+        a.stride = p.stride;
+        a.zero_diag = h->zero_diag;
+        a.replicas = it.replicas;
+        a.sweep_begin = 0;
+        a.sweep_end = it.sweeps;
+        a.key0 = (uint32_t)it.seed;
+        a.key1 = (uint32_t)(it.seed >> 32);
+        a.inst = it.instance_id;
+        a.mode = 0;
+        a.beta = it.beta;
+        a.fresh = 1;
+        a.perm = w.perm;
+        a.best_perm = w.best_perm;
+        a.energy = w.energy;
+        a.best_energy = w.best_energy;
+        a.best_sweep = w.best_sweep;
+        a.accepted = w.accepted;
+        a.rung = w.rung;
+        a.tables = w.tables;
+        a.status = w.status;
+        a.df_bytes = p.df_bytes;
+        a.group_bytes = p.group_bytes;
+        a.sv_len = p.sv_len;
+        a.groups = p.groups;
+        a.target = it.target;
+        a.reach_ns = (unsigned long long *)it.reach_ns;
+        a.reach_sweep = it.reach_sweep;
+        a.done = w.done;
+        a.stop = (it.target && (flags & PDIT_BATCH_STOP_AT_TARGET)) ? 1 : 0;
+        outs[k] = BatchOut{it.best_perm, it.best_cost, h->n, it.replicas, w.best_energy, w.best_perm};
+    }
+    // Units, per class ordered by decreasing cost (sweeps x n^3 per unit).
+    for (size_t c = 0; c < b->classes.size() && rc == PDIT_OK; ++c) {
+        BatchClass &x = b->classes[c];
+        std::vector<int> order = x.items;
+        std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+            const double cu = (double)items[u].sweeps * std::pow((double)items[u].qap->n, 3.0);
+            const double cv = (double)items[v].sweeps * std::pow((double)items[v].qap->n, 3.0);
+            return cu > cv;
+        });
+        std::vector<pdit::BatchUnit> units;
+        for (int k : order)
+            for (int r0 = 0; r0 < items[k].replicas; r0 += plans[k].groups) units.push_back(pdit::BatchUnit{k, r0});
+        x.nunits = (int)units.size();
+        e = cudaMalloc((void **)&x.d_units, sizeof(pdit::BatchUnit) * units.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(x.d_units, units.data(), sizeof(pdit::BatchUnit) * units.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "pdit_batch_create");
+            break;
+        }
+        int bps = 0;
+        const int qe = batch_blocks(x.dt, x, &bps);
+        if (qe != 0) {
+            rc = cuda_fail((cudaError_t)qe, "batch occupancy query");
+            break;
+        }
+        if (bps < 1) bps = 1;
+        const int sms = items[x.items[0]].qap->num_sms;
+        x.grid = std::max(1, std::min(x.nunits, sms * bps));
+    }
+    if (rc == PDIT_OK) {
+        e = cudaMemcpy(b->d_descs, descs.data(), sizeof(pdit::SweepArgs) * count, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_outs, outs.data(), sizeof(BatchOut) * count, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(e, "pdit_batch_create");
+    }
+    if (rc) {
+        pdit_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return PDIT_OK;
+}
+
+int pdit_batch_run(pdit_batch *b, void *stream) {
+    if (!b) return PDIT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(b->flags & PDIT_BATCH_GRAPH)) return batch_enqueue(b, st);
+    if (!st) return PDIT_EINVAL;  // the legacy default stream cannot be captured
+    if (!b->exec) {
+        PDIT_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const int rc = batch_enqueue(b, st);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        const cudaError_t ie = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            b->exec = nullptr;
+            return cuda_fail(ie, "cudaGraphInstantiate");
+        }
+    }
+    PDIT_CK(cudaGraphLaunch(b->exec, st));
+    return PDIT_OK;
+}
+
+int pdit_batch_info(const pdit_batch *b, int *classes, size_t *workspace_bytes) {
+    if (!b) return PDIT_EINVAL;
+    if (classes) *classes = (int)b->classes.size();
+    if (workspace_bytes) *workspace_bytes = b->ws_bytes;
     return PDIT_OK;
 }
 

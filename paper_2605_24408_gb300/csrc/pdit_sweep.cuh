@@ -59,10 +59,17 @@ struct SweepArgs {
     int32_t *dump;         // optional [replicas][n][n]: final tables
     int *queue;            // work counter, zero at launch
     int *status;           // audit bits
+    // time-to-target bookkeeping (all optional, per instance)
+    const int64_t *target;      // record the first time best <= *target
+    unsigned long long *reach_ns;  // atomicMin of %globaltimer at that moment
+    int *reach_sweep;           // atomicMin of the sweep index (-1 = initial state)
+    int *done;                  // set once reached; replicas stop at their next sweep if stop
+    int stop;                   // stop replicas of an instance whose target was reached
     // launch shape
     size_t df_bytes;       // bytes of staged D and F (16-byte multiple)
     size_t group_bytes;    // bytes of one group's slice
     int sv_len;            // int32 entries of the scratch vector (multiple of 4)
+    int groups;            // replica groups per CTA (multi-instance launches)
 };
 
 // Per-group scratch for cross-warp reductions and broadcasts.
@@ -71,7 +78,7 @@ struct GroupScratch {
     int wmin[8];
     int sel_j, sel_d;
     int item;
-    int pad;
+    int stop;
 };
 constexpr size_t kScratchBytes = sizeof(GroupScratch);  // 112
 
@@ -178,6 +185,21 @@ __device__ __forceinline__ void group_sync(int bar) {
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// First time this replica's best reaches the instance target: record when.
+__device__ __forceinline__ void note_target(const SweepArgs &a, long long bestE, int sweep, bool &reached) {
+    if (reached || !a.target || bestE > *a.target) return;
+    reached = true;
+    if (a.reach_ns) atomicMin(a.reach_ns, global_ns());
+    if (a.reach_sweep) atomicMin(a.reach_sweep, sweep);
+    if (a.done) atomicExch(a.done, 1);
+}
+
 __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
     x.x += u * v.x;
     x.y += u * v.y;
@@ -276,12 +298,14 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     }
     long long E, bestE, acc_moves;
     int bsweep;
+    bool reached = false;
     if (a.fresh) {
         E = esum;
         bestE = esum;
         bsweep = -1;
         acc_moves = 0;
         for (int m = t; m < n; m += G) gbp[m] = sp[m];
+        if (t == 0) note_target(a, bestE, -1, reached);
     } else {
         E = a.energy[r];
         bestE = a.best_energy[r];
@@ -340,6 +364,14 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     };
 
     for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
+        if (a.stop) {
+            // group-uniform decision from one read of the instance's flag
+            if (t == 0) gs->stop = *reinterpret_cast<volatile int *>(a.done);
+            group_sync<WPR>(bar);
+            const int stop_now = gs->stop;
+            group_sync<WPR>(bar);
+            if (stop_now) break;
+        }
         const float beta = a.mode != 0 ? beta_fixed : a.beta[s];
         for (int i0 = 0; i0 < n; i0 += 32) {
             // Philox(inst, replica, sweep, location) for the next 32 locations.
@@ -562,6 +594,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     bestE = E;
                     bsweep = s;
                     for (int m = t; m < n; m += G) gbp[m] = m == i ? fb : (m == js ? fa : sp[m]);
+                    if (t == 0) note_target(a, bestE, s, reached);
                 }
                 group_sync<WPR>(bar);
             }
@@ -651,6 +684,71 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(
     }
 }
 
+// One unit of a multi-instance launch: replicas r0 .. r0 + groups - 1 of
+// one instance, run by the groups of one CTA.
+struct BatchUnit {
+    int inst;
+    int r0;
+};
+
+// Persistent multi-instance kernel: CTAs take units from `queue`; D and F are
+// restaged when the CTA moves to another instance. Every instance of a launch
+// shares the compiled shape (DT, MAXK, WPR, TSMEM, PK).
+template <typename DT, int MAXK, int WPR, bool TSMEM, int PK>
+__global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
+    batch_kernel(const SweepArgs *__restrict__ descs, const BatchUnit *__restrict__ units, int nunits,
+                 int *queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SweepArgs sa;
+    __shared__ int s_unit;
+    constexpr int G = 32 * WPR;
+    const int grp = threadIdx.x / G;
+    const int t = threadIdx.x % G;
+    const int bar = 1 + grp;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(queue, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= nunits) break;
+        const BatchUnit bu = units[u];
+        if (bu.inst != cur) {
+            // descriptor and matrices of the new instance
+            const int *src = reinterpret_cast<const int *>(descs + bu.inst);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+            const int n = descs[bu.inst].n;
+            const int32_t *D = descs[bu.inst].D, *F = descs[bu.inst].F;
+            DT *sD = reinterpret_cast<DT *>(smem);
+            DT *sF = sD + n * n;
+            for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+                sD[idx] = static_cast<DT>(D[idx]);
+                sF[idx] = static_cast<DT>(F[idx]);
+            }
+            cur = bu.inst;
+        }
+        __syncthreads();
+        const int n = sa.n;
+        const int r = bu.r0 + grp;
+        if (grp < sa.groups && r < sa.replicas) {
+            const DT *sD = reinterpret_cast<const DT *>(smem);
+            const DT *sF = sD + n * n;
+            unsigned char *gb = smem + sa.df_bytes + (size_t)grp * sa.group_bytes;
+            const int npad = (n + 3) & ~3;
+            GroupScratch *gs = reinterpret_cast<GroupScratch *>(gb);
+            unsigned char *body = gb + kScratchBytes;
+            int32_t *sT = reinterpret_cast<int32_t *>(body);
+            int32_t *sp = reinterpret_cast<int32_t *>(body + (TSMEM ? (size_t)n * sa.stride * 4 : 0));
+            int32_t *sh = sp + npad;
+            int32_t *sv = sh + npad;
+            uint32_t *upk = reinterpret_cast<uint32_t *>(sv + sa.sv_len);
+            uint32_t *vpk = upk + npad;
+            int32_t *T = TSMEM ? sT : sa.tables + (size_t)r * n * sa.stride;
+            run_replica<DT, MAXK, WPR, PK>(sa, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
+        }
+    }
+}
+
 // Host-side entry points, one per storage type of D and F (defined in
 // pdit_sweep_i8.cu, pdit_sweep_i16.cu, pdit_sweep_i32.cu). Return a
 // cudaError_t value; cudaErrorInvalidValue for a shape with no kernel.
@@ -659,17 +757,22 @@ int sweep_blocks_per_sm(int maxk, int wpr, bool tsmem, int pk, int threads, size
 template <typename DT>
 int sweep_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid, int threads,
                  size_t smem, cudaStream_t stream);
+template <typename DT>
+int batch_blocks_per_sm(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, int *blocks);
+template <typename DT>
+int batch_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *descs, const BatchUnit *units,
+                 int nunits, int *queue, int grid, int threads, size_t smem, cudaStream_t stream);
 
 // Shapes with a compiled kernel: (MAXK, WPR) with 32 * WPR * MAXK in
-// {32, 64, 128, 256}; the global-table variant only for 256; deferred
-// updates (PK = 4) only with tables in shared memory.
+// {32, 64, 128, 256}; the global-table variant only for 256.
 #define PDIT_SWEEP_SHAPES_COMMON(X)                                                              \
     X(1, 1, true, 1) X(2, 1, true, 1) X(1, 2, true, 1) X(4, 1, true, 1) X(2, 2, true, 1)         \
     X(1, 4, true, 1) X(8, 1, true, 1) X(4, 2, true, 1) X(2, 4, true, 1) X(1, 8, true, 1)         \
     X(8, 1, false, 1) X(4, 2, false, 1) X(2, 4, false, 1) X(1, 8, false, 1)
 #define PDIT_SWEEP_SHAPES_DEFERRED(X)                                                            \
     X(1, 1, true, 4) X(2, 1, true, 4) X(1, 2, true, 4) X(4, 1, true, 4) X(2, 2, true, 4)         \
-    X(1, 4, true, 4) X(8, 1, true, 4) X(4, 2, true, 4) X(2, 4, true, 4) X(1, 8, true, 4)
+    X(1, 4, true, 4) X(8, 1, true, 4) X(4, 2, true, 4) X(2, 4, true, 4) X(1, 8, true, 4)         \
+    X(8, 1, false, 4) X(4, 2, false, 4) X(2, 4, false, 4) X(1, 8, false, 4)
 
 #define PDIT_INSTANTIATE_SWEEP(DT, SHAPES)                                                       \
     template <int MAXK, int WPR, bool TSMEM, int PK>                                             \
@@ -702,11 +805,46 @@ int sweep_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int 
     int sweep_launch<DT>(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid,    \
                          int threads, size_t smem, cudaStream_t st) {                            \
         return sweep_dispatch(maxk, wpr, tsmem, pk, a, grid, threads, smem, st, nullptr, false); \
+    }                                                                                            \
+    template <int MAXK, int WPR, bool TSMEM, int PK>                                             \
+    static int batch_one(const SweepArgs *d, const BatchUnit *u, int nu, int *q, int grid,       \
+                         int threads, size_t smem, cudaStream_t st, int *blocks, bool query) {   \
+        auto fn = batch_kernel<DT, MAXK, WPR, TSMEM, PK>;                                        \
+        if (threads > SweepBounds<MAXK, WPR>::threads) return (int)cudaErrorInvalidValue;        \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                             (int)smem);                                         \
+        if (e != cudaSuccess) return (int)e;                                                     \
+        if (query) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn,         \
+                                                                              threads, smem);    \
+        fn<<<grid, threads, smem, st>>>(d, u, nu, q);                                            \
+        return (int)cudaGetLastError();                                                          \
+    }                                                                                            \
+    static int batch_dispatch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *d,         \
+                              const BatchUnit *u, int nu, int *q, int grid, int threads,         \
+                              size_t smem, cudaStream_t st, int *blocks, bool query) {           \
+        SHAPES(PDIT_BATCH_CASE)                                                                  \
+        return (int)cudaErrorInvalidValue;                                                       \
+    }                                                                                            \
+    template <>                                                                                  \
+    int batch_blocks_per_sm<DT>(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, \
+                                int *blocks) {                                                   \
+        return batch_dispatch(maxk, wpr, tsmem, pk, nullptr, nullptr, 0, nullptr, 0, threads,    \
+                              smem, nullptr, blocks, true);                                      \
+    }                                                                                            \
+    template <>                                                                                  \
+    int batch_launch<DT>(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *d,              \
+                         const BatchUnit *u, int nu, int *q, int grid, int threads, size_t smem, \
+                         cudaStream_t st) {                                                      \
+        return batch_dispatch(maxk, wpr, tsmem, pk, d, u, nu, q, grid, threads, smem, st,        \
+                              nullptr, false);                                                   \
     }
 
 #define PDIT_CASE(MK, W, TS, K)                                                                  \
     if (maxk == MK && wpr == W && tsmem == TS && pk == K)                                        \
         return sweep_one<MK, W, TS, K>(a, grid, threads, smem, st, blocks, query);
+#define PDIT_BATCH_CASE(MK, W, TS, K)                                                            \
+    if (maxk == MK && wpr == W && tsmem == TS && pk == K)                                        \
+        return batch_one<MK, W, TS, K>(d, u, nu, q, grid, threads, smem, st, blocks, query);
 
 #define PDIT_SWEEP_SHAPES_ALL(X) PDIT_SWEEP_SHAPES_COMMON(X) PDIT_SWEEP_SHAPES_DEFERRED(X)
 

@@ -30,6 +30,8 @@ PDIT_MODE_ANNEAL = 0
 PDIT_MODE_PT = 1
 PDIT_MODE_FIXED = 2
 PDIT_FLAG_RESUME = 1
+PDIT_BATCH_STOP_AT_TARGET = 1
+PDIT_BATCH_GRAPH = 2
 
 _lib = None
 
@@ -73,6 +75,26 @@ class pdit_opts(ctypes.Structure):
         ("replica_rung", ctypes.c_void_p),
         ("tables", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
+        ("target", ctypes.c_void_p),
+        ("reach_ns", ctypes.c_void_p),
+        ("reach_sweep", ctypes.c_void_p),
+        ("stop_at_target", ctypes.c_int),
+    ]
+
+
+class pdit_batch_item(ctypes.Structure):
+    _fields_ = [
+        ("qap", ctypes.c_void_p),
+        ("replicas", ctypes.c_int),
+        ("sweeps", ctypes.c_int),
+        ("beta", ctypes.c_void_p),
+        ("seed", ctypes.c_uint64),
+        ("instance_id", ctypes.c_uint32),
+        ("best_perm", ctypes.c_void_p),
+        ("best_cost", ctypes.c_void_p),
+        ("target", ctypes.c_void_p),
+        ("reach_ns", ctypes.c_void_p),
+        ("reach_sweep", ctypes.c_void_p),
     ]
 
 
@@ -118,6 +140,15 @@ def lib():
     L.pdit_anneal_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_uint64,
                                       vp, vp, vp]
     L.pdit_anneal_noalloc.restype = ctypes.c_int
+    L.pdit_batch_create.argtypes = [ctypes.POINTER(pdit_batch_item), ctypes.c_int, ctypes.c_uint32,
+                                    ctypes.POINTER(vp)]
+    L.pdit_batch_create.restype = ctypes.c_int
+    L.pdit_batch_run.argtypes = [vp, vp]
+    L.pdit_batch_run.restype = ctypes.c_int
+    L.pdit_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
+    L.pdit_batch_info.restype = ctypes.c_int
+    L.pdit_batch_destroy.argtypes = [vp]
+    L.pdit_batch_destroy.restype = None
     L.pdit_strerror.argtypes = [ctypes.c_int]
     L.pdit_strerror.restype = ctypes.c_char_p
     L.pdit_last_error.argtypes = []
@@ -293,7 +324,7 @@ def anneal_device(q: Qap, replicas: int, beta, sweeps: int, seed: int, *, mode: 
                   ladder_len: int = 0, exchange_period: int = 4, timeout_periods: int = 100,
                   instance_id: int = 0, replica_base: int = 0, sweep_begin: int = 0,
                   sweep_end: int = -1, resume: bool = False, workspace=None, per_replica: bool = False,
-                  tables: bool = False, stream=None):
+                  tables: bool = False, stream=None, target=None, stop_at_target: bool = False):
     """pdit_anneal_ex on torch device tensors. `beta` is a CUDA float32 tensor.
     Returns a dict of device tensors (asynchronous on the current stream)."""
     import torch
@@ -314,6 +345,9 @@ def anneal_device(q: Qap, replicas: int, beta, sweeps: int, seed: int, *, mode: 
             out["replica_rung"] = torch.empty(R, dtype=torch.int32, device=dev)
     if tables:
         out["tables"] = torch.empty(R, n, n, dtype=torch.int32, device=dev)
+    if target is not None:
+        out["reach_ns"] = torch.empty(1, dtype=torch.int64, device=dev)
+        out["reach_sweep"] = torch.empty(1, dtype=torch.int32, device=dev)
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     o = opts(replicas=R, sweeps=sweeps, seed=seed & 0xFFFFFFFFFFFFFFFF, instance_id=instance_id,
              replica_base=replica_base, mode=mode, beta=beta.data_ptr(), ladder_len=ladder_len,
@@ -327,6 +361,72 @@ def anneal_device(q: Qap, replicas: int, beta, sweeps: int, seed: int, *, mode: 
     o.workspace_bytes = workspace.numel()
     for k, t in out.items():
         setattr(o, k, t.data_ptr())
+    if target is not None:
+        o.target = target.data_ptr()
+        o.stop_at_target = 1 if stop_at_target else 0
     pdit_anneal_ex(q, o)
     out["workspace"] = workspace
     return out
+
+
+# --- multi-instance batches ----------------------------------------------------
+
+class Batch:
+    """pdit_batch_create / pdit_batch_run / pdit_batch_destroy over torch device
+    tensors. items: list of dicts with keys qap, replicas, sweeps, beta (CUDA
+    float32 tensor), seed, instance_id, and optional target (CUDA int64 [1])."""
+
+    def __init__(self, items, stop_at_target: bool = False, graph: bool = False):
+        import torch
+
+        self.items = items
+        arr = (pdit_batch_item * len(items))()
+        self.out = []
+        for k, it in enumerate(items):
+            q = it["qap"]
+            dev = it["beta"].device
+            o = {"best_perm": torch.empty(q.n, dtype=torch.int32, device=dev),
+                 "best_cost": torch.empty(1, dtype=torch.int64, device=dev)}
+            if it.get("target") is not None:
+                o["reach_ns"] = torch.empty(1, dtype=torch.int64, device=dev)
+                o["reach_sweep"] = torch.empty(1, dtype=torch.int32, device=dev)
+            self.out.append(o)
+            e = arr[k]
+            e.qap = q.handle.value
+            e.replicas = it["replicas"]
+            e.sweeps = it["sweeps"]
+            e.beta = it["beta"].data_ptr()
+            e.seed = it.get("seed", 0) & 0xFFFFFFFFFFFFFFFF
+            e.instance_id = it.get("instance_id", 0)
+            e.best_perm = o["best_perm"].data_ptr()
+            e.best_cost = o["best_cost"].data_ptr()
+            if it.get("target") is not None:
+                e.target = it["target"].data_ptr()
+                e.reach_ns = o["reach_ns"].data_ptr()
+                e.reach_sweep = o["reach_sweep"].data_ptr()
+        flags = (PDIT_BATCH_STOP_AT_TARGET if stop_at_target else 0) | (PDIT_BATCH_GRAPH if graph else 0)
+        h = ctypes.c_void_p()
+        _check(lib().pdit_batch_create(arr, len(items), flags, ctypes.byref(h)), "pdit_batch_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        import torch
+
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().pdit_batch_run(self.handle, ctypes.c_void_p(st.cuda_stream)), "pdit_batch_run")
+
+    def info(self):
+        c, w = ctypes.c_int(), ctypes.c_size_t()
+        _check(lib().pdit_batch_info(self.handle, ctypes.byref(c), ctypes.byref(w)), "pdit_batch_info")
+        return int(c.value), int(w.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pdit_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
