@@ -196,13 +196,123 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_ragged(args):
+    """Ragged multi-instance batch: K instances, N uniform in 12..256 (half grid
+    D with 30% flow density, half dense 0..99), R replicas and S linear sweeps
+    each. (A) one batched, graph-captured run to the end: throughput and each
+    instance's final best C_k. Targets T_k = floor(1.01 C_k). Time to reach
+    every target with each instance's replicas stopping once its target is
+    reached: (B) batched, (C) one single-instance launch after another."""
+    import torch
+
+    from paper_2605_24408_gb300 import build as B
+    from paper_2605_24408_gb300 import pdit as P
+
+    torch.cuda.set_device(0)
+    B.build()
+    dev = torch.device("cuda", 0)
+    K, R, S = args.instances, args.ragged_replicas, args.ragged_sweeps
+    qs, betas, sizes = [], [], []
+    for k in range(K):
+        n = G.ragged_size(k, 0)
+        D, F = G.ragged_instance(k, n, 0)
+        q = P.Qap(D, F)
+        qs.append(q)
+        sizes.append(n)
+        betas.append(torch.from_numpy(P.pdit_beta_schedule("linear", S, P.pdit_beta_max(q))).to(dev))
+    # autotune one instance per distinct size, reuse its shape for the others
+    tuned = {}
+    t0 = time.perf_counter()
+    if not args.no_autotune:
+        for k, q in enumerate(qs):
+            n = sizes[k]
+            if n not in tuned:
+                mid = torch.full((4,), float(betas[k][S // 2].item()), dtype=torch.float32, device=dev)
+                tuned[n] = P.pdit_autotune(q, R, mid, 4)
+            else:
+                P.pdit_set_warps_per_replica(q, tuned[n][0])
+                P.pdit_set_pending_swaps(q, tuned[n][1])
+    tune_s = time.perf_counter() - t0
+    items = [dict(qap=q, replicas=R, sweeps=S, beta=betas[k], seed=0, instance_id=k) for k, q in enumerate(qs)]
+    stream = torch.cuda.Stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+        stream.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1000.0
+
+    full = P.Batch(items, graph=True)
+    with torch.cuda.stream(stream):
+        full.run(stream)  # capture + first run
+    stream.synchronize()
+    t_full = timed(lambda: full.run(stream))
+    best = [int(o["best_cost"].item()) for o in full.out]
+    updates = sum(n * R * S for n in sizes)
+    targets = [torch.tensor([int(c * 1.01)], dtype=torch.int64, device=dev) for c in best]
+    titems = [dict(it, target=targets[k]) for k, it in enumerate(items)]
+    bt = P.Batch(titems, stop_at_target=True, graph=True)
+    with torch.cuda.stream(stream):
+        bt.run(stream)
+    stream.synchronize()
+    t_batched = timed(lambda: bt.run(stream))
+    reached_b = sum(int(o["reach_sweep"].item()) < S for o in bt.out)
+    # plain: one launch per instance, in sequence, same targets and stopping
+    ws = []
+    for k, q in enumerate(qs):
+        o = P.opts(replicas=R, sweeps=S, seed=0, instance_id=k, beta=betas[k].data_ptr(),
+                   stream=stream.cuda_stream, stop_at_target=1, target=targets[k].data_ptr())
+        w = torch.empty(P.pdit_workspace_bytes(q, o), dtype=torch.uint8, device=dev)
+        outs = {"best_perm": torch.empty(q.n, dtype=torch.int32, device=dev),
+                "best_cost": torch.empty(1, dtype=torch.int64, device=dev),
+                "reach_ns": torch.empty(1, dtype=torch.int64, device=dev),
+                "reach_sweep": torch.empty(1, dtype=torch.int32, device=dev)}
+        o.workspace, o.workspace_bytes = w.data_ptr(), w.numel()
+        for key, t in outs.items():
+            setattr(o, key, t.data_ptr())
+        ws.append((o, w, outs))
+
+    def plain():
+        for k, q in enumerate(qs):
+            P.pdit_anneal_ex(q, ws[k][0])
+
+    with torch.cuda.stream(stream):
+        plain()
+    stream.synchronize()
+    t_plain = timed(plain)
+    reached_p = sum(int(w[2]["reach_sweep"].item()) < S for w in ws)
+    classes, wsb = full.info()
+    line = {"metric": "time-to-1%-gap, ragged batch", "value": t_batched, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "int32",
+            "config": {"workload": "ragged: %d instances, N uniform 12..256 (even k grid D + 30%% flow "
+                                   "1..10, odd k dense 0..99), %d replicas x %d linear sweeps each"
+                                   % (K, R, S),
+                       "target": "1.01 x the final best of the full batched run (same random streams)",
+                       "autotune": not args.no_autotune, "autotune_s": tune_s,
+                       "shape_classes": classes, "workspace_bytes": wsb},
+            "batched_s": t_batched, "plain_s": t_plain, "speedup": t_plain / t_batched,
+            "instances_reached": {"batched": reached_b, "plain": reached_p},
+            "full_run": {"seconds": t_full, "updates": updates, "updates_per_s": updates / t_full}}
+    print(json.dumps(line), flush=True)
+    for q in qs:
+        q.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS) + ["ragged"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--ragged-replicas", type=int, default=256)
+    ap.add_argument("--ragged-sweeps", type=int, default=2000)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--wpr", type=int, default=0,
@@ -213,7 +323,9 @@ def main():
                     help="override the workload's sweep count (smaller cases for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
-        return run_reference(args, args.workload)
+        return run_reference(args, args.workload if args.workload != "ragged" else "n100")
+    if args.workload == "ragged":
+        return run_ragged(args)
 
     import torch
 

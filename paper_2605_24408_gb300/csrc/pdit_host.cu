@@ -18,6 +18,7 @@ struct pdit_qap {
     int device = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
+    size_t l2_bytes = 0;
     int dt_bytes = 4;       // storage of D and F in shared memory: 1, 2 or 4 bytes
     int zero_diag = 0;
     int packed_ok = 0;      // max-min of D and of F <= 127: swap factors fit int8
@@ -119,18 +120,26 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     if (pk != 0 && pk != 1 && pk != 4) return PDIT_EINVAL;
     if (pk == 4 && !defer_ok) return PDIT_ENOTSUP;
     if (pk == 0) {
-        // Defer table rewrites when the ring costs no replica slot.
+        // Defer table rewrites when the packed factors cost no replica slot
+        // (tables in shared memory), and always for tables in global memory.
         pk = 1;
         if (defer_ok) {
             const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1);
             const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4);
-            if ((budget - p->df_bytes) / g4 == (budget - p->df_bytes) / g1) pk = 4;
+            if (!p->tsmem || (budget - p->df_bytes) / g4 == (budget - p->df_bytes) / g1) pk = 4;
         }
     }
     p->pk = pk;
     p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk);
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
-    const int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
+    int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
+    if (!p->tsmem && h->l2_bytes > 0 && h->num_sms > 0) {
+        // Tables in global memory: keep the tables of all resident replicas
+        // within three quarters of L2 (one CTA per SM).
+        const size_t table = (size_t)4 * n * p->stride;
+        const int cap = (int)std::max<size_t>(1, (h->l2_bytes * 3 / 4) / (table * (size_t)h->num_sms));
+        fit = std::min(fit, cap);
+    }
     if (wpr <= 0) {
         // Aim for about 16 resident warps per SM to hide the latency of each
         // replica's sequential update chain.
@@ -151,6 +160,7 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     int e = sweep_blocks(h->dt_bytes, *p, &bps);
     if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
     if (bps < 1) bps = 1;
+    if (!p->tsmem) bps = 1;
     const int need = (replicas + g - 1) / g;
     p->grid = std::max(1, std::min(need, h->num_sms * bps));
     return PDIT_OK;
@@ -372,6 +382,8 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     h->smem_optin = (size_t)v;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, h->device);
+    h->l2_bytes = (size_t)v;
     const size_t bytes = sizeof(int32_t) * (size_t)n * n;
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dD, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dF, bytes);
@@ -635,6 +647,68 @@ int pdit_beta_max(const pdit_qap *h, double *beta_max) {
             }
         }
     *beta_max = cnt ? 10.0 / (sum / (double)cnt) : 1.0;
+    return PDIT_OK;
+}
+
+int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int *shape) {
+    if (!h || replicas < 1 || sweeps < 1 || !beta) return PDIT_EINVAL;
+    if (!h->stream) PDIT_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    const int cover = cover_for(h->n);
+    const int keep_wpr = h->force_wpr, keep_pk = h->force_pk;
+    int32_t *dperm = nullptr;
+    int64_t *dcost = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc((void **)&dperm, sizeof(int32_t) * h->n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dcost, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best_wpr = 0, best_pk = 0, rc = PDIT_OK;
+    float best_ms = 0.0f;
+    for (int wpr = 1; wpr <= cover / 32 && wpr <= 8 && e == cudaSuccess && rc == PDIT_OK; wpr <<= 1)
+        for (int pk = 1; pk <= 4 && e == cudaSuccess && rc == PDIT_OK; pk += 3) {
+            h->force_wpr = wpr;
+            h->force_pk = pk;
+            Plan p;
+            if (make_plan(h, replicas, wpr, pk, &p) != PDIT_OK) continue;
+            pdit_opts o;
+            pdit_opts_init(&o);
+            o.replicas = replicas;
+            o.sweeps = sweeps;
+            o.seed = 0x5EED;
+            o.beta = beta;
+            o.stream = h->stream;
+            o.best_perm = dperm;
+            o.best_cost = dcost;
+            rc = pdit_anneal_ex(h, &o);  // warm-up (and workspace)
+            if (rc) break;
+            e = cudaEventRecord(e0, h->stream);
+            if (e == cudaSuccess) rc = pdit_anneal_ex(h, &o);
+            if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && !rc && (best_wpr == 0 || ms < best_ms)) {
+                best_ms = ms;
+                best_wpr = wpr;
+                best_pk = pk;
+            }
+        }
+    cudaFree(dperm);
+    cudaFree(dcost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc || e != cudaSuccess || best_wpr == 0) {
+        h->force_wpr = keep_wpr;
+        h->force_pk = keep_pk;
+        if (rc) return rc;
+        return e != cudaSuccess ? cuda_fail(e, "pdit_autotune") : PDIT_ENOTSUP;
+    }
+    h->force_wpr = best_wpr;
+    h->force_pk = best_pk;
+    if (shape) {
+        shape[0] = best_wpr;
+        shape[1] = best_pk;
+    }
     return PDIT_OK;
 }
 
@@ -1154,6 +1228,7 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
             break;
         }
         if (bps < 1) bps = 1;
+        if (!x.tsmem) bps = 1;
         const int sms = items[x.items[0]].qap->num_sms;
         x.grid = std::max(1, std::min(x.nunits, sms * bps));
     }

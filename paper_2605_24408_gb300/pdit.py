@@ -140,6 +140,8 @@ def lib():
     L.pdit_anneal_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_uint64,
                                       vp, vp, vp]
     L.pdit_anneal_noalloc.restype = ctypes.c_int
+    L.pdit_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp]
+    L.pdit_autotune.restype = ctypes.c_int
     L.pdit_batch_create.argtypes = [ctypes.POINTER(pdit_batch_item), ctypes.c_int, ctypes.c_uint32,
                                     ctypes.POINTER(vp)]
     L.pdit_batch_create.restype = ctypes.c_int
@@ -250,6 +252,15 @@ def pdit_set_warps_per_replica(q: Qap, wpr: int):
 
 def pdit_set_pending_swaps(q: Qap, k: int):
     _check(lib().pdit_set_pending_swaps(q.handle, k), "pdit_set_pending_swaps")
+
+
+def pdit_autotune(q: Qap, replicas: int, beta, sweeps: int) -> tuple[int, int]:
+    """Time the valid shapes on a short run (beta: CUDA float32 tensor of >= sweeps
+    values) and keep the fastest on the handle. Returns (warps per replica, pending swaps)."""
+    out = np.zeros(2, dtype=np.int32)
+    _check(lib().pdit_autotune(q.handle, replicas, ctypes.c_void_p(beta.data_ptr()), sweeps, _ptr(out)),
+           "pdit_autotune")
+    return int(out[0]), int(out[1])
 
 
 def pdit_launch_shape(q: Qap, replicas: int) -> dict:
