@@ -302,13 +302,115 @@ def run_ragged(args):
         q.close()
 
 
+def run_served(args):
+    """Serving with continuous batching. Request r: N uniform in 20..200 from
+    r, the ragged generator keyed by r, 512 replicas, 2000 linear sweeps.
+    (1) capacity: a closed burst of requests; (2) an open-loop Poisson stream
+    at a fraction of that capacity for a fixed window: p50/p99 latency (submit
+    to result) and solves/s. The configured 200 requests/s is reported as the
+    offered load beside the capacity."""
+    import threading
+
+    import torch
+
+    from paper_2605_24408_gb300 import build as B
+    from paper_2605_24408_gb300 import pdit as P
+
+    torch.cuda.set_device(0)
+    B.build()
+    R, S = args.serve_replicas, args.serve_sweeps
+    reqs = {}
+
+    def instance(rid):
+        if rid not in reqs:
+            reqs[rid] = G.request_instance(rid)
+        return reqs[rid]
+
+    def drain(srv, tickets, producer=None):
+        while True:
+            a, q = srv.tick()
+            if (producer is None or not producer.is_alive()) and a == 0 and q == 0:
+                break
+        out = []
+        for rid, t in tickets.items():
+            st, _, cost, lat = srv.result(t)
+            out.append((rid, st, cost, lat))
+        return out
+
+    # (1) capacity: a burst submitted at once
+    srv = P.Server(device_budget_bytes=args.serve_budget_gb << 30, slice_sweeps=args.serve_slice,
+                   max_active=args.serve_max_active)
+    burst = args.serve_burst
+    for rid in range(burst):
+        instance(rid)
+    t0 = time.perf_counter()
+    tickets = {rid: srv.submit(*instance(rid), R, S, 0, rid) for rid in range(burst)}
+    res = drain(srv, tickets)
+    t_burst = time.perf_counter() - t0
+    srv.close()
+    capacity = burst / t_burst
+    upd = sum(instance(rid)[0].shape[0] * R * S for rid in range(burst))
+    # (2) open-loop Poisson arrivals at a fraction of capacity
+    lam = args.serve_load * capacity
+    gaps = -np.log(1.0 - G.hash_unit(7, 91, np.arange(100000, dtype=np.uint64))) / lam
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < args.serve_window]
+    base = 1000
+    for k in range(len(arrivals)):
+        instance(base + k)
+    srv = P.Server(device_budget_bytes=args.serve_budget_gb << 30, slice_sweeps=args.serve_slice,
+                   max_active=args.serve_max_active)
+    tickets = {}
+
+    def producer():
+        start = time.perf_counter()
+        for k, at in enumerate(arrivals):
+            delay = at - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[base + k] = srv.submit(*instance(base + k), R, S, 0, base + k)
+
+    th = threading.Thread(target=producer)
+    t0 = time.perf_counter()
+    th.start()
+    res2 = drain(srv, tickets, th)
+    th.join()
+    t_open = time.perf_counter() - t0
+    srv.close()
+    lats = np.array([r[3] for r in res2 if r[1] == 2])
+    line = {"metric": "p50/p99 latency, served stream", "value": float(np.percentile(lats, 50)) if len(lats) else None,
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "int32",
+            "config": {"workload": "served: request r -> N uniform 20..200 (ragged generator keyed by r), "
+                                   "%d replicas x %d linear sweeps per request" % (R, S),
+                       "slice_sweeps": args.serve_slice, "max_active": args.serve_max_active,
+                       "device_budget_gb": args.serve_budget_gb},
+            "capacity": {"burst_requests": burst, "seconds": t_burst, "solves_per_s": capacity,
+                         "updates_per_s": upd / t_burst},
+            "open_loop": {"arrival_rate_per_s": lam, "load_fraction_of_capacity": args.serve_load,
+                          "window_s": args.serve_window, "requests": int(len(arrivals)),
+                          "completed": int(len(lats)), "p50_s": float(np.percentile(lats, 50)) if len(lats) else None,
+                          "p99_s": float(np.percentile(lats, 99)) if len(lats) else None,
+                          "solves_per_s": len(lats) / t_open},
+            "offered_rate_configured_per_s": 200.0,
+            "offered_over_capacity": 200.0 / capacity}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS) + ["ragged"])
+    ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS) + ["ragged", "served"])
+    ap.add_argument("--serve-replicas", type=int, default=512)
+    ap.add_argument("--serve-sweeps", type=int, default=2000)
+    ap.add_argument("--serve-slice", type=int, default=100)
+    ap.add_argument("--serve-max-active", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=int, default=16)
+    ap.add_argument("--serve-burst", type=int, default=24)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-window", type=float, default=20.0)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--ragged-replicas", type=int, default=256)
     ap.add_argument("--ragged-sweeps", type=int, default=2000)
@@ -323,9 +425,11 @@ def main():
                     help="override the workload's sweep count (smaller cases for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
-        return run_reference(args, args.workload if args.workload != "ragged" else "n100")
+        return run_reference(args, args.workload if args.workload in WORKLOADS else "n100")
     if args.workload == "ragged":
         return run_ragged(args)
+    if args.workload == "served":
+        return run_served(args)
 
     import torch
 

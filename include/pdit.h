@@ -93,6 +93,18 @@ int qap_n(const pdit_qap *h);
 int pdit_set_warps_per_replica(pdit_qap *h, int wpr);
 
 /*
+ * pdit_autotune -- time every compiled thread mapping (warps per replica)
+ * and table-update batching (1 or 4 pending swaps) valid for this instance
+ * on a short run of `replicas` chains over the DEVICE schedule beta[sweeps]
+ * (CUDA events on the handle's stream), keep the fastest for later calls on
+ * this handle and write it to shape[0] (warps per replica) and shape[1]
+ * (pending swaps) when shape is not NULL. Synchronous; allocates and frees
+ * small temporary buffers. Results of later calls do not depend on the
+ * choice. Errors: PDIT_EINVAL, PDIT_ENOTSUP, PDIT_ECUDA.
+ */
+int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int *shape);
+
+/*
  * pdit_launch_shape -- the sweep-kernel launch a call with `replicas` chains
  * would use: shape[0] warps per replica, [1] candidates per thread, [2]
  * replicas per CTA, [3] CTAs, [4] 1 if the influence tables live in shared
@@ -328,6 +340,58 @@ int pdit_batch_info(const pdit_batch *b, int *classes, size_t *workspace_bytes);
 
 /* pdit_batch_destroy -- free the batch (not the instances). NULL-safe. */
 void pdit_batch_destroy(pdit_batch *b);
+
+/*
+ * Serving with continuous batching. Requests (one QAP instance each) are
+ * submitted from any host thread; pdit_server_tick, called in a loop by one
+ * thread, admits queued requests in arrival order while active slots and the
+ * device-memory budget allow (each request's footprint: its matrices,
+ * replica state and schedule), runs the next `slice_sweeps` sweeps of every
+ * active request in one batched launch per kernel shape (replica state stays
+ * on the device between slices; a slice resumes exactly where the previous
+ * one stopped), and retires the requests whose schedule has ended. A
+ * request's result is the same as a single pdit_anneal_ex call with
+ * instance_id = its request id: alone or in any mix.
+ */
+typedef struct pdit_server pdit_server;
+
+/*
+ * pdit_server_create -- device_budget_bytes: device memory the admitted
+ * requests may hold together (one oversize request is still admitted when
+ * nothing else is active); slice_sweeps: sweeps per tick (>= 1);
+ * max_active: requests resident at once. Errors: PDIT_EINVAL, PDIT_ECUDA.
+ */
+int pdit_server_create(size_t device_budget_bytes, int slice_sweeps, int max_active, pdit_server **out);
+
+/*
+ * pdit_server_submit -- queue one request: host D, F (n x n int32,
+ * symmetric, copied), replicas, sweeps, seed, request_id (Philox counter
+ * word 0), and beta (host [sweeps]; NULL = the linear schedule
+ * 0 -> pdit_beta_max). Thread-safe. *ticket identifies the request.
+ * Errors: PDIT_EINVAL, PDIT_ENOMEM.
+ */
+int pdit_server_submit(pdit_server *s, int n, const int32_t *D, const int32_t *F, int replicas, int sweeps,
+                       uint64_t seed, uint32_t request_id, const float *beta, int64_t *ticket);
+
+/*
+ * pdit_server_tick -- one scheduling step (admit, one slice for every
+ * active request, retire). Synchronous on the server's own stream.
+ * Reports how many requests are active and queued afterwards.
+ * Errors: PDIT_EINVAL, PDIT_ECUDA, PDIT_ENOTSUP.
+ */
+int pdit_server_tick(pdit_server *s, int *active, int *queued);
+
+/*
+ * pdit_server_result -- state of a request (0 queued, 1 running, 2 done,
+ * 3 failed at admission); when done, its best permutation (host [n]), best
+ * cost and latency (seconds from submit to the end of its last slice).
+ * Thread-safe. Errors: PDIT_EINVAL.
+ */
+int pdit_server_result(pdit_server *s, int64_t ticket, int *state, int32_t *best_perm, int64_t *best_cost,
+                       double *latency_s);
+
+/* pdit_server_destroy -- free the server and every request. NULL-safe. */
+void pdit_server_destroy(pdit_server *s);
 
 /* pdit_strerror -- static text for an error code. */
 const char *pdit_strerror(int code);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -1275,6 +1276,394 @@ int pdit_batch_info(const pdit_batch *b, int *classes, size_t *workspace_bytes) 
     if (!b) return PDIT_EINVAL;
     if (classes) *classes = (int)b->classes.size();
     if (workspace_bytes) *workspace_bytes = b->ws_bytes;
+    return PDIT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving loop with continuous batching.
+// ---------------------------------------------------------------------------
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServerRequest {
+    int64_t ticket = 0;
+    uint32_t request_id = 0;
+    int n = 0, replicas = 0, sweeps = 0;
+    uint64_t seed = 0;
+    std::vector<int32_t> D, F;
+    std::vector<float> beta;  // host schedule until admission
+    pdit_qap *qap = nullptr;
+    void *ws = nullptr;
+    float *dbeta = nullptr;
+    int32_t *dperm = nullptr;
+    int64_t *dcost = nullptr;
+    Plan plan;
+    Workspace w{};
+    size_t footprint = 0;
+    int done_sweeps = 0;
+    int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+    double t_submit = 0, t_done = 0;
+    std::vector<int32_t> perm;
+    int64_t cost = 0;
+};
+
+}  // namespace
+
+struct pdit_server {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    int slice = 100, max_active = 64;
+    std::mutex mu;
+    std::vector<ServerRequest *> all;   // by ticket
+    std::vector<ServerRequest *> queue; // FIFO of queued tickets
+    std::vector<ServerRequest *> active;
+    // per-tick device/host staging (grown on demand)
+    pdit::SweepArgs *d_descs = nullptr, *h_descs = nullptr;
+    BatchOut *d_outs = nullptr, *h_outs = nullptr;
+    pdit::BatchUnit *d_units = nullptr, *h_units = nullptr;
+    int *d_queues = nullptr;
+    size_t cap_desc = 0, cap_units = 0;
+    std::vector<BatchClass> classes;  // streams and events reused
+    cudaStream_t main = nullptr;
+    cudaEvent_t fork = nullptr;
+    int64_t completed = 0;
+};
+
+namespace {
+
+void release_request(pdit_server *s, ServerRequest *r) {
+    cudaFree(r->ws);
+    cudaFree(r->dbeta);
+    cudaFree(r->dperm);
+    cudaFree(r->dcost);
+    r->ws = nullptr;
+    r->dbeta = nullptr;
+    r->dperm = nullptr;
+    r->dcost = nullptr;
+    qap_destroy(r->qap);
+    r->qap = nullptr;
+    s->used -= std::min(s->used, r->footprint);
+}
+
+// Device memory a request holds while admitted.
+size_t request_footprint(const ServerRequest &r, const Plan &p) {
+    pdit_opts o;
+    pdit_opts_init(&o);
+    o.replicas = r.replicas;
+    return carve(r.qap, &o, p, nullptr).bytes + (size_t)8 * r.n * r.n + 4 * (size_t)r.sweeps + 4 * r.n + 8 + 1024;
+}
+
+int admit(pdit_server *s, ServerRequest *r) {
+    int rc = qap_create(r->n, r->D.data(), r->F.data(), &r->qap);
+    if (rc) return rc;
+    rc = make_plan(r->qap, 1 << 28, 0, 0, &r->plan, kBatchStaticSmem);
+    if (rc) return rc;
+    const size_t fp = request_footprint(*r, r->plan);
+    if (s->used + fp > s->budget && !s->active.empty()) return 1;  // wait for memory
+    if (r->beta.empty()) {
+        double bmax = 0.0;
+        pdit_beta_max(r->qap, &bmax);
+        r->beta.resize((size_t)std::max(r->sweeps, 1));
+        pdit_beta_schedule(0, r->sweeps, bmax, r->beta.data());
+    }
+    pdit_opts o;
+    pdit_opts_init(&o);
+    o.replicas = r->replicas;
+    const size_t wsb = carve(r->qap, &o, r->plan, nullptr).bytes;
+    cudaError_t e = cudaMalloc(&r->ws, wsb);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&r->dbeta, sizeof(float) * std::max(r->sweeps, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&r->dperm, sizeof(int32_t) * r->n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&r->dcost, sizeof(int64_t));
+    if (e == cudaSuccess && r->sweeps > 0)
+        e = cudaMemcpyAsync(r->dbeta, r->beta.data(), sizeof(float) * r->sweeps, cudaMemcpyHostToDevice, s->main);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PDIT_ENOMEM : cuda_fail(e, "server admit");
+    r->w = carve(r->qap, &o, r->plan, (char *)r->ws);
+    r->footprint = fp;
+    s->used += fp;
+    r->D.clear();
+    r->D.shrink_to_fit();
+    r->F.clear();
+    r->F.shrink_to_fit();
+    r->state = 1;
+    return PDIT_OK;
+}
+
+int grow(pdit_server *s, size_t ndesc, size_t nunits) {
+    if (ndesc > s->cap_desc) {
+        cudaFree(s->d_descs);
+        cudaFreeHost(s->h_descs);
+        cudaFree(s->d_outs);
+        cudaFreeHost(s->h_outs);
+        s->d_descs = nullptr;
+        s->h_descs = nullptr;
+        s->d_outs = nullptr;
+        s->h_outs = nullptr;
+        const size_t c = std::max(ndesc, (size_t)64);
+        PDIT_CK(cudaMalloc((void **)&s->d_descs, sizeof(pdit::SweepArgs) * c));
+        PDIT_CK(cudaMallocHost((void **)&s->h_descs, sizeof(pdit::SweepArgs) * c));
+        PDIT_CK(cudaMalloc((void **)&s->d_outs, sizeof(BatchOut) * c));
+        PDIT_CK(cudaMallocHost((void **)&s->h_outs, sizeof(BatchOut) * c));
+        s->cap_desc = c;
+    }
+    if (nunits > s->cap_units) {
+        cudaFree(s->d_units);
+        cudaFreeHost(s->h_units);
+        s->d_units = nullptr;
+        s->h_units = nullptr;
+        const size_t c = std::max(nunits * 2, (size_t)1024);
+        PDIT_CK(cudaMalloc((void **)&s->d_units, sizeof(pdit::BatchUnit) * c));
+        PDIT_CK(cudaMallocHost((void **)&s->h_units, sizeof(pdit::BatchUnit) * c));
+        s->cap_units = c;
+    }
+    return PDIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdit_server_create(size_t device_budget_bytes, int slice_sweeps, int max_active, pdit_server **out) {
+    if (!out) return PDIT_EINVAL;
+    *out = nullptr;
+    if (device_budget_bytes == 0 || slice_sweeps < 1 || max_active < 1) return PDIT_EINVAL;
+    pdit_server *s = new (std::nothrow) pdit_server();
+    if (!s) return PDIT_ENOMEM;
+    s->budget = device_budget_bytes;
+    s->slice = slice_sweeps;
+    s->max_active = max_active;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_queues, sizeof(int) * 64);
+    if (e != cudaSuccess) {
+        const int rc = cuda_fail(e, "pdit_server_create");
+        pdit_server_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return PDIT_OK;
+}
+
+void pdit_server_destroy(pdit_server *s) {
+    if (!s) return;
+    if (s->main) cudaStreamSynchronize(s->main);
+    for (ServerRequest *r : s->all) {
+        release_request(s, r);
+        delete r;
+    }
+    for (BatchClass &c : s->classes) {
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    cudaFree(s->d_descs);
+    cudaFreeHost(s->h_descs);
+    cudaFree(s->d_outs);
+    cudaFreeHost(s->h_outs);
+    cudaFree(s->d_units);
+    cudaFreeHost(s->h_units);
+    cudaFree(s->d_queues);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->main) cudaStreamDestroy(s->main);
+    delete s;
+}
+
+int pdit_server_submit(pdit_server *s, int n, const int32_t *D, const int32_t *F, int replicas, int sweeps,
+                       uint64_t seed, uint32_t request_id, const float *beta, int64_t *ticket) {
+    if (!s || !ticket || n < 2 || n > PDIT_N_MAX || !D || !F || replicas < 1 || sweeps < 0) return PDIT_EINVAL;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (D[(size_t)i * n + j] != D[(size_t)j * n + i] || F[(size_t)i * n + j] != F[(size_t)j * n + i])
+                return PDIT_EINVAL;
+    ServerRequest *r = new (std::nothrow) ServerRequest();
+    if (!r) return PDIT_ENOMEM;
+    r->request_id = request_id;
+    r->n = n;
+    r->replicas = replicas;
+    r->sweeps = sweeps;
+    r->seed = seed;
+    r->D.assign(D, D + (size_t)n * n);
+    r->F.assign(F, F + (size_t)n * n);
+    if (beta && sweeps > 0) r->beta.assign(beta, beta + sweeps);
+    r->t_submit = now_s();
+    std::lock_guard<std::mutex> lock(s->mu);
+    r->ticket = (int64_t)s->all.size();
+    s->all.push_back(r);
+    s->queue.push_back(r);
+    *ticket = r->ticket;
+    return PDIT_OK;
+}
+
+int pdit_server_tick(pdit_server *s, int *active, int *queued) {
+    if (!s) return PDIT_EINVAL;
+    // 1. admit queued requests (FIFO) while slots and device memory allow
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+            ServerRequest *r = s->queue.front();
+            const int rc = admit(s, r);
+            if (rc == 1) {  // does not fit yet: release what admit created, retry later
+                qap_destroy(r->qap);
+                r->qap = nullptr;
+                break;
+            }
+            s->queue.erase(s->queue.begin());
+            if (rc) {
+                r->state = 3;
+                release_request(s, r);
+                continue;
+            }
+            s->active.push_back(r);
+        }
+    }
+    const int na = (int)s->active.size();
+    if (na > 0) {
+        // 2. one slice of sweeps for every active request, one launch per kernel shape
+        size_t nunits = 0;
+        for (ServerRequest *r : s->active) nunits += (size_t)(r->replicas + r->plan.groups - 1) / r->plan.groups;
+        int rc = grow(s, (size_t)na, nunits);
+        if (rc) return rc;
+        std::vector<BatchClass> cls;
+        std::vector<std::vector<int>> members;
+        for (int k = 0; k < na; ++k) {
+            ServerRequest *r = s->active[k];
+            const Plan &p = r->plan;
+            pdit::SweepArgs &a = s->h_descs[k];
+            a = pdit::SweepArgs{};
+            a.D = r->qap->dD;
+            a.F = r->qap->dF;
+            a.n = r->n;
+            a.stride = p.stride;
+            a.zero_diag = r->qap->zero_diag;
+            a.replicas = r->replicas;
+            a.sweep_begin = r->done_sweeps;
+            a.sweep_end = std::min(r->sweeps, r->done_sweeps + s->slice);
+            a.key0 = (uint32_t)r->seed;
+            a.key1 = (uint32_t)(r->seed >> 32);
+            a.inst = r->request_id;
+            a.beta = r->dbeta;
+            a.fresh = r->done_sweeps == 0 ? 1 : 0;
+            a.perm = r->w.perm;
+            a.best_perm = r->w.best_perm;
+            a.energy = r->w.energy;
+            a.best_energy = r->w.best_energy;
+            a.best_sweep = r->w.best_sweep;
+            a.accepted = r->w.accepted;
+            a.rung = r->w.rung;
+            a.tables = r->w.tables;
+            a.status = r->w.status;
+            a.df_bytes = p.df_bytes;
+            a.group_bytes = p.group_bytes;
+            a.sv_len = p.sv_len;
+            a.groups = p.groups;
+            s->h_outs[k] = BatchOut{r->dperm, r->dcost, r->n, r->replicas, r->w.best_energy, r->w.best_perm};
+            const int dt = r->qap->dt_bytes;
+            int found = -1;
+            for (size_t c = 0; c < cls.size(); ++c)
+                if (cls[c].dt == dt && cls[c].maxk == p.maxk && cls[c].wpr == p.wpr && cls[c].pk == p.pk &&
+                    cls[c].tsmem == p.tsmem)
+                    found = (int)c;
+            if (found < 0) {
+                BatchClass x;
+                x.dt = dt;
+                x.maxk = p.maxk;
+                x.wpr = p.wpr;
+                x.pk = p.pk;
+                x.tsmem = p.tsmem;
+                cls.push_back(x);
+                members.emplace_back();
+                found = (int)cls.size() - 1;
+            }
+            cls[found].threads = std::max(cls[found].threads, p.threads);
+            cls[found].smem = std::max(cls[found].smem, p.smem);
+            members[found].push_back(k);
+        }
+        if (cls.size() > 64) return PDIT_ENOTSUP;
+        while (s->classes.size() < cls.size()) {
+            BatchClass c;
+            PDIT_CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+            PDIT_CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+            s->classes.push_back(c);
+        }
+        size_t u = 0;
+        for (size_t c = 0; c < cls.size(); ++c) {
+            std::vector<int> order = members[c];
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                const ServerRequest *a = s->active[x], *b = s->active[y];
+                return (double)a->n * a->n * a->n > (double)b->n * b->n * b->n;
+            });
+            cls[c].d_units = s->d_units + u;
+            const size_t u0 = u;
+            for (int k : order)
+                for (int r0 = 0; r0 < s->active[k]->replicas; r0 += s->active[k]->plan.groups)
+                    s->h_units[u++] = pdit::BatchUnit{k, r0};
+            cls[c].nunits = (int)(u - u0);
+            cls[c].stream = s->classes[c].stream;
+            cls[c].done = s->classes[c].done;
+            int bps = 0;
+            const int qe = batch_blocks(cls[c].dt, cls[c], &bps);
+            if (qe != 0) return cuda_fail((cudaError_t)qe, "server occupancy query");
+            if (bps < 1 || !cls[c].tsmem) bps = 1;
+            cls[c].grid = std::max(1, std::min(cls[c].nunits, s->active[members[c][0]]->qap->num_sms * bps));
+        }
+        PDIT_CK(cudaMemcpyAsync(s->d_descs, s->h_descs, sizeof(pdit::SweepArgs) * na, cudaMemcpyHostToDevice, s->main));
+        PDIT_CK(cudaMemcpyAsync(s->d_units, s->h_units, sizeof(pdit::BatchUnit) * u, cudaMemcpyHostToDevice, s->main));
+        PDIT_CK(cudaMemcpyAsync(s->d_outs, s->h_outs, sizeof(BatchOut) * na, cudaMemcpyHostToDevice, s->main));
+        PDIT_CK(cudaMemsetAsync(s->d_queues, 0, sizeof(int) * cls.size(), s->main));
+        PDIT_CK(cudaEventRecord(s->fork, s->main));
+        for (size_t c = 0; c < cls.size(); ++c) {
+            PDIT_CK(cudaStreamWaitEvent(cls[c].stream, s->fork, 0));
+            const int e = batch_launch(cls[c], s->d_descs, s->d_queues + c);
+            if (e != 0) return cuda_fail((cudaError_t)e, "server batch launch");
+            PDIT_CK(cudaEventRecord(cls[c].done, cls[c].stream));
+            PDIT_CK(cudaStreamWaitEvent(s->main, cls[c].done, 0));
+        }
+        // 3. results of the requests whose schedule ends with this slice
+        batch_finalize_kernel<<<na, 256, 0, s->main>>>(s->d_outs);
+        PDIT_CK(cudaGetLastError());
+        std::vector<ServerRequest *> finishing;
+        for (ServerRequest *r : s->active) {
+            r->done_sweeps = std::min(r->sweeps, r->done_sweeps + s->slice);
+            if (r->done_sweeps >= r->sweeps) {
+                r->perm.resize((size_t)r->n);
+                PDIT_CK(cudaMemcpyAsync(r->perm.data(), r->dperm, sizeof(int32_t) * r->n, cudaMemcpyDeviceToHost, s->main));
+                PDIT_CK(cudaMemcpyAsync(&r->cost, r->dcost, sizeof(int64_t), cudaMemcpyDeviceToHost, s->main));
+                finishing.push_back(r);
+            }
+        }
+        PDIT_CK(cudaStreamSynchronize(s->main));
+        const double t = now_s();
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (ServerRequest *r : finishing) {
+            r->t_done = t;
+            r->state = 2;
+            release_request(s, r);
+            s->completed += 1;
+            s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+        }
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (active) *active = (int)s->active.size();
+    if (queued) *queued = (int)s->queue.size();
+    return PDIT_OK;
+}
+
+int pdit_server_result(pdit_server *s, int64_t ticket, int *state, int32_t *best_perm, int64_t *best_cost,
+                       double *latency_s) {
+    if (!s || !state) return PDIT_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (ticket < 0 || ticket >= (int64_t)s->all.size()) return PDIT_EINVAL;
+    const ServerRequest *r = s->all[(size_t)ticket];
+    *state = r->state;
+    if (r->state == 2) {
+        if (best_perm) std::memcpy(best_perm, r->perm.data(), sizeof(int32_t) * r->n);
+        if (best_cost) *best_cost = r->cost;
+        if (latency_s) *latency_s = r->t_done - r->t_submit;
+    }
     return PDIT_OK;
 }
 

@@ -152,3 +152,10 @@ def random_symmetric(n: int, lo: int, hi: int, seed: int, tag: int, diag: bool =
     if diag:
         m[np.arange(n), np.arange(n)] = hash_int(seed, tag + 7, np.arange(n, dtype=np.uint64), lo, hi)
     return m.astype(np.int32)
+
+
+def request_instance(request_id: int, lo: int = 20, hi: int = 200):
+    """The instance of a serving request: N uniform in lo..hi from the request
+    id, then the ragged-batch generator keyed by the request id."""
+    n = int(hash_int(request_id, 81, np.uint64(0), lo, hi))
+    return ragged_instance(request_id, n, request_id)

@@ -151,6 +151,18 @@ def lib():
     L.pdit_batch_info.restype = ctypes.c_int
     L.pdit_batch_destroy.argtypes = [vp]
     L.pdit_batch_destroy.restype = None
+    L.pdit_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+    L.pdit_server_create.restype = ctypes.c_int
+    L.pdit_server_submit.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.c_uint32, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.pdit_server_submit.restype = ctypes.c_int
+    L.pdit_server_tick.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.pdit_server_tick.restype = ctypes.c_int
+    L.pdit_server_result.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), vp,
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    L.pdit_server_result.restype = ctypes.c_int
+    L.pdit_server_destroy.argtypes = [vp]
+    L.pdit_server_destroy.restype = None
     L.pdit_strerror.argtypes = [ctypes.c_int]
     L.pdit_strerror.restype = ctypes.c_char_p
     L.pdit_last_error.argtypes = []
@@ -434,6 +446,59 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             lib().pdit_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- serving ---------------------------------------------------------------------
+
+class Server:
+    """pdit_server_*: continuous-batching request loop (see include/pdit.h)."""
+
+    def __init__(self, device_budget_bytes: int = 8 << 30, slice_sweeps: int = 100, max_active: int = 64):
+        h = ctypes.c_void_p()
+        _check(lib().pdit_server_create(device_budget_bytes, slice_sweeps, max_active, ctypes.byref(h)),
+               "pdit_server_create")
+        self.handle = h
+        self.n = {}
+
+    def submit(self, D, F, replicas: int, sweeps: int, seed: int, request_id: int, beta=None) -> int:
+        D = np.ascontiguousarray(D, dtype=np.int32)
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float32)
+        t = ctypes.c_int64()
+        _check(lib().pdit_server_submit(self.handle, D.shape[0], _ptr(D), _ptr(F), replicas, sweeps,
+                                        seed & 0xFFFFFFFFFFFFFFFF, request_id,
+                                        _ptr(b) if b is not None else None, ctypes.byref(t)),
+               "pdit_server_submit")
+        self.n[int(t.value)] = D.shape[0]
+        return int(t.value)
+
+    def tick(self):
+        a, q = ctypes.c_int(), ctypes.c_int()
+        _check(lib().pdit_server_tick(self.handle, ctypes.byref(a), ctypes.byref(q)), "pdit_server_tick")
+        return int(a.value), int(q.value)
+
+    def result(self, ticket: int):
+        """(state, perm or None, cost or None, latency or None)."""
+        st = ctypes.c_int()
+        perm = np.zeros(self.n[ticket], dtype=np.int32)
+        cost = ctypes.c_int64()
+        lat = ctypes.c_double()
+        _check(lib().pdit_server_result(self.handle, ticket, ctypes.byref(st), _ptr(perm), ctypes.byref(cost),
+                                        ctypes.byref(lat)), "pdit_server_result")
+        if st.value != 2:
+            return int(st.value), None, None, None
+        return 2, perm, int(cost.value), float(lat.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pdit_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
