@@ -65,6 +65,14 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def survey_bytes_per_update(n: int, accept_frac: float) -> float:
+    """Algorithmic shared-memory bytes per p-dit update of the method as
+    written (every accepted swap rewrites the table): 4 (4N) for the gathers
+    (row, column, p-diagonal, permutation, int32) plus, per accepted swap,
+    8 N^2 (table read and write) + 8 N (the two factor vectors)."""
+    return 4 * (4 * n) + accept_frac * (8 * n * n + 8 * n)
+
+
 def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pending: int = 1) -> float:
     """Shared-memory bytes one update must move in this design.
     Immediate table updates (pending = 1):
@@ -549,7 +557,8 @@ def main():
     # roofline of the sweep kernel: shared-memory bound
     props = torch.cuda.get_device_properties(dev)
     dt_bytes = 1 if max(abs(int(D.max())), abs(int(F.max()))) <= 127 else 2
-    bpu = algorithmic_bytes_per_update(n, dt_bytes, accept_frac, shape["pending_swaps"])
+    bpu = survey_bytes_per_update(n, accept_frac)
+    bpu_design = algorithmic_bytes_per_update(n, dt_bytes, accept_frac, shape["pending_swaps"])
     kernel_s = tot_ms / 1000.0 / args.steps
     achieved = bpu * upd_rank / kernel_s / 1e9
     sm_mhz = clk.get("sm_mhz") or 0.0
@@ -586,6 +595,10 @@ def main():
                                                                    "smem" if shape["tables_in_smem"] else "global",
                                                                    shape["pending_swaps"]),
                      "bytes_per_update": bpu,
+                     "bytes_per_update_basis": "16 N + A (8 N^2 + 8 N): the method's traffic with a table "
+                                               "rewrite per accepted swap",
+                     "design_bytes_per_update": bpu_design,
+                     "design_frac": (bpu_design * upd_rank / kernel_s / 1e9 / peak) if peak else None,
                      "peak_source": "derived: %d SMs x %d B/clk x median SM clock under load (%s MHz)"
                                     % (props.multi_processor_count, SMEM_BYTES_PER_CLK, sm_mhz)},
         "wall_s_timed_region": wall,
