@@ -427,6 +427,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--wpr", type=int, default=0,
                     help="warps per replica (0: the library's choice)")
+    ap.add_argument("--mode", default="anneal", choices=["anneal", "cupim"],
+                    help="sequential p-dit sweeps (the paper's PIM) or concurrent updates (its CUPIM)")
     ap.add_argument("--pk", type=int, default=0,
                     help="accepted swaps held before a table rewrite (0: the library's choice)")
     ap.add_argument("--sweeps", type=int, default=0,
@@ -481,7 +483,7 @@ def main():
             "replica_accepted": torch.empty(replicas, dtype=torch.int64, device=dev),
             "status": torch.zeros(1, dtype=torch.int32, device=dev)}
     o = P.opts(replicas=replicas, sweeps=sweeps, seed=0, replica_base=base, beta=dbeta.data_ptr(),
-               stream=stream.cuda_stream)
+               stream=stream.cuda_stream, mode=P.PDIT_MODE_CUPIM if args.mode == "cupim" else P.PDIT_MODE_ANNEAL)
     ws = torch.empty(P.pdit_workspace_bytes(q, o), dtype=torch.uint8, device=dev)
     o.workspace, o.workspace_bytes = ws.data_ptr(), ws.numel()
     for k, t in outs.items():
@@ -578,6 +580,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "%s: dense symmetric QAP N=%d (D, F uniform 0..99)" % (args.workload, n)
                    if args.workload == "n100" else args.workload,
+                   "mode": args.mode,
                    "replicas_per_gpu": replicas, "sweeps": sweeps, "schedule": kind, "seed": 0,
                    "global_batch": replicas * world, "seq_len": n,
                    "parallelism": "replicas sharded over %d GPU(s)" % world,

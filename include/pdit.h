@@ -52,6 +52,7 @@ extern "C" {
 #define PDIT_MODE_ANNEAL 0 /* beta[s] for sweep s, every replica */
 #define PDIT_MODE_PT 1     /* parallel tempering over a beta ladder */
 #define PDIT_MODE_FIXED 2  /* beta[r] for replica r, every sweep, no exchange (beta-range trials) */
+#define PDIT_MODE_CUPIM 3  /* concurrent updates from a snapshot (GPU-CUPIM Algorithm section), beta[s] */
 
 /* Flags. */
 #define PDIT_FLAG_RESUME 1u /* continue from the replica state already in the workspace */
@@ -156,7 +157,7 @@ typedef struct pdit_opts {
     uint64_t seed;          /* Philox key */
     uint32_t instance_id;   /* Philox counter word 0; default 0 */
     uint32_t replica_base;  /* global id of this call's replica 0 (counter word 1); default 0 */
-    int mode;               /* PDIT_MODE_ANNEAL (default), PDIT_MODE_PT or PDIT_MODE_FIXED */
+    int mode;               /* PDIT_MODE_ANNEAL (default), _PT, _FIXED or _CUPIM (one iteration per sweep) */
     const float *beta;      /* anneal: [sweeps]; PT: [ladder_len], rung 0 = smallest beta; fixed: [replicas] */
     int ladder_len;         /* PT: replicas per set (2..64); replicas % ladder_len == 0 */
     int exchange_period;    /* PT: sweeps between exchanges (paper: 4) */

@@ -200,7 +200,8 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
     """Runs replicas [rep_begin, rep_end). mode 'anneal': beta[s] per sweep;
     mode 'pt': beta is the ladder (rung 0 = smallest beta), sets of ladder_len
     consecutive replicas exchange every `period` sweeps; mode 'fixed':
-    beta[k] for the k-th replica of the call, no exchange."""
+    beta[k] for the k-th replica of the call, no exchange; mode 'cupim':
+    concurrent updates, beta[s] per iteration."""
     D, F = _i32(D), _i32(F)
     n = D.shape[0]
     R = rep_end - rep_begin
@@ -213,7 +214,7 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
     rung = np.zeros(R, np.int32) if mode == "pt" else None
     reach = np.zeros(R, np.int32) if target is not None else None
     rc = lib().oracle_anneal(
-        n, D, F, rep_begin, rep_end, {"anneal": 0, "pt": 1, "fixed": 2}[mode], ladder_len, period, timeout,
+        n, D, F, rep_begin, rep_end, {"anneal": 0, "pt": 1, "fixed": 2, "cupim": 3}[mode], ladder_len, period, timeout,
         beta, sweeps, seed, inst, threads, out["final_perm"], out["final_cost"],
         out["best_perm"], out["best_cost"], out["best_sweep"], out["accepted"],
         nb.ctypes.data if nb is not None else None,

@@ -32,6 +32,8 @@
  *                         reading R7).
  *   oracle_philox4x32_10  Salmon, Moraes, Dror, Shaw, "Parallel random
  *                         numbers: as easy as 1, 2, 3", SC'11 (reading R5).
+ *   cupim_iteration       the concurrent-update variant (GPU-CUPIM Algorithm
+ *                         section; reading R12).
  *   oracle_brute_force    min over all N! permutations of Eq. 1.
  *
  * Pins (tests/test_oracle_*.py): Eq. 1 on a hand-worked 3-facility case and
@@ -347,7 +349,7 @@ typedef struct {
     int n;
     const int32_t *D, *F;
     int rep_begin, rep_end;   /* replicas [rep_begin, rep_end) */
-    int mode;                 /* 0: anneal with beta[sweep]; 1: PT with beta[rung]; 2: beta[replica] */
+    int mode;                 /* 0: anneal beta[sweep]; 1: PT beta[rung]; 2: beta[replica]; 3: concurrent updates, beta[sweep] */
     int ladder_len, period, timeout;
     const float *beta;        /* anneal: [sweeps]; PT: [ladder_len] */
     int sweeps;
@@ -368,6 +370,70 @@ typedef struct {
     int32_t *reach;       /* [R] or NULL: that sweep (-1 = initial state), INT32_MAX if never */
     int status;
 } anneal_job_t;
+
+/* ------------------------------------------------------------------------ */
+/* Concurrent updates (GPU-CUPIM Algorithm section; reading R12). One        */
+/* iteration: (1) every location i draws a proposal j_i from Eq. 5 over the   */
+/* swap energies of the current state (a snapshot: nothing changes while the  */
+/* proposals are drawn), with the draw of location i in that iteration;      */
+/* (2) the proposals that move (j_i != i) are ranked by their snapshot energy */
+/* change, ascending, ties to the lower initiating location, and accepted in */
+/* that order when neither of their two locations is taken yet (a pair       */
+/* proposed from both ends is accepted once); losers stay; (3) the accepted   */
+/* swaps are applied in that order, each with its exact energy change on the  */
+/* then-current table (Eq. 3) and the incremental influence update.          */
+/* Returns the number of swaps applied.                                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int i, j;
+    int64_t dE;
+} proposal_t;
+
+static int proposal_before(const proposal_t *x, const proposal_t *y) {
+    return x->dE < y->dE || (x->dE == y->dE && x->i < y->i);
+}
+
+static int cupim_iteration(replica_t *X, float beta, uint64_t seed, uint32_t inst, uint32_t rep,
+                           uint32_t sweep) {
+    const int n = X->n;
+    proposal_t *prop = (proposal_t *)malloc(sizeof(proposal_t) * (size_t)n);
+    int64_t *dE = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int np = 0;
+    for (int i = 0; i < n; ++i) {
+        uint64_t r = oracle_update_draw(seed, inst, rep, sweep, (uint32_t)i);
+        int j = oracle_choose(X, i, beta, r, dE, NULL, NULL);
+        if (j != i) {
+            prop[np].i = i;
+            prop[np].j = j;
+            prop[np].dE = dE[j];
+            ++np;
+        }
+    }
+    /* insertion sort by (dE, i) */
+    for (int a = 1; a < np; ++a) {
+        proposal_t key = prop[a];
+        int b = a - 1;
+        while (b >= 0 && proposal_before(&key, &prop[b])) {
+            prop[b + 1] = prop[b];
+            --b;
+        }
+        prop[b + 1] = key;
+    }
+    unsigned char *taken = (unsigned char *)calloc((size_t)n, 1);
+    int applied = 0;
+    for (int a = 0; a < np; ++a) {
+        int i = prop[a].i, j = prop[a].j;
+        if (taken[i] || taken[j]) continue;
+        taken[i] = taken[j] = 1;
+        int64_t d = oracle_delta_e(n, X->D, X->F, X->p, X->I, i, j);
+        apply_choice(X, i, j, d);
+        ++applied;
+    }
+    free(taken);
+    free(prop);
+    free(dE);
+    return applied;
+}
 
 static void run_job(anneal_job_t *J) {
     const int n = J->n;
@@ -400,6 +466,17 @@ static void run_job(anneal_job_t *J) {
             replica_t *X = &reps[k];
             uint32_t rep = (uint32_t)(J->rep_begin + k);
             float beta = J->mode == 1 ? J->beta[rung[k]] : J->mode == 2 ? J->beta[k] : J->beta[s];
+            if (J->mode == 3) {
+                J->accepted[k] += cupim_iteration(X, beta, J->seed, J->inst, rep, (uint32_t)s);
+                if (X->E < J->best_E[k]) {
+                    J->best_E[k] = X->E;
+                    J->best_sweep[k] = s;
+                    memcpy(J->best_p + (size_t)k * n, X->p, sizeof(int32_t) * (size_t)n);
+                    if (J->reach && J->has_target && J->reach[k] == 0x7FFFFFFF && X->E <= J->target)
+                        J->reach[k] = s;
+                }
+                continue;
+            }
             for (int i = 0; i < n; ++i) {
                 uint64_t r = oracle_update_draw(J->seed, J->inst, rep, (uint32_t)s, (uint32_t)i);
                 int64_t *dE = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);

@@ -74,7 +74,7 @@ int cover_for(int n) {
 struct Plan {
     int maxk = 1, wpr = 1, pk = 1;
     bool tsmem = true;
-    int stride = 0, sv_len = 0;
+    int stride = 0, sv_len = 0, cupim_off = 0;
     size_t df_bytes = 0, group_bytes = 0, smem = 0;
     int groups = 1, threads = 32, grid = 1;
 };
@@ -98,9 +98,9 @@ int sv_len_for(int stride, int cover) { return std::max(stride, cover); }
 // Shared-memory slice of one replica group for a given shape: scratch
 // struct, table (if in shared memory), p, h, the scratch vector, and the
 // packed pending swap factors (int8 x 4 per word) when pk > 1.
-size_t group_bytes_for(int n, int stride, int cover, bool tsmem, int pk) {
+size_t group_bytes_for(int n, int stride, int cover, bool tsmem, int pk, int extra_sv = 0) {
     const size_t npad = (size_t)((n + 3) & ~3);
-    const size_t vec = 4 * (2 * npad + (size_t)sv_len_for(stride, cover));
+    const size_t vec = 4 * (2 * npad + (size_t)sv_len_for(stride, cover) + (size_t)extra_sv);
     const size_t table = tsmem ? (size_t)4 * n * stride : 0;
     const size_t ring = pk > 1 ? (size_t)8 * npad : 0;  // packed u and v words
     return align_up(pdit::kScratchBytes + table + vec + ring, 16);
@@ -108,14 +108,18 @@ size_t group_bytes_for(int n, int stride, int cover, bool tsmem, int pk) {
 
 // Launch shape for `replicas` chains of an n-location instance. `wpr` = warps
 // per replica (0: choose).
-int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t reserve = 0) {
+int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t reserve = 0,
+              bool cupim = false) {
     const int n = h->n;
     const int cover = cover_for(n);
     p->stride = table_stride(n);
     p->sv_len = sv_len_for(p->stride, cover);
+    p->cupim_off = p->sv_len;
+    if (cupim) p->sv_len += 3 * ((n + 3) & ~3);  // proposal, energy change, order
     p->df_bytes = align_up((size_t)2 * n * n * h->dt_bytes, 16);
     const size_t budget = h->smem_optin - reserve;
-    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1) <= budget;
+    const int extra = p->sv_len - sv_len_for(p->stride, cover);
+    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1, extra) <= budget;
     if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;
     const bool defer_ok = h->packed_ok != 0;
     if (pk != 0 && pk != 1 && pk != 4) return PDIT_EINVAL;
@@ -125,13 +129,13 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
         // (tables in shared memory), and always for tables in global memory.
         pk = 1;
         if (defer_ok) {
-            const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1);
-            const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4);
+            const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1, extra);
+            const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4, extra);
             if (!p->tsmem || (budget - p->df_bytes) / g4 == (budget - p->df_bytes) / g1) pk = 4;
         }
     }
     p->pk = pk;
-    p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk);
+    p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk, extra);
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
     int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
     if (!p->tsmem && h->l2_bytes > 0 && h->num_sms > 0) {
@@ -308,7 +312,7 @@ int validate_opts(const pdit_qap *h, const pdit_opts *o) {
     if ((uint64_t)o->sweeps >= 0xFFFFFFFFull) return PDIT_EINVAL;
     if (!o->best_perm || !o->best_cost) return PDIT_EINVAL;
     if (se > o->sweep_begin && !o->beta) return PDIT_EINVAL;
-    if (o->mode != PDIT_MODE_ANNEAL && o->mode != PDIT_MODE_PT && o->mode != PDIT_MODE_FIXED) return PDIT_EINVAL;
+    if (o->mode < PDIT_MODE_ANNEAL || o->mode > PDIT_MODE_CUPIM) return PDIT_EINVAL;
     if (o->mode == PDIT_MODE_PT) {
         if (o->ladder_len < 2 || o->ladder_len > 64 || o->replicas % o->ladder_len) return PDIT_EINVAL;
         if (o->exchange_period < 1 || o->timeout_periods < 0) return PDIT_EINVAL;
@@ -449,7 +453,7 @@ int pdit_set_pending_swaps(pdit_qap *h, int k) {
 size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o) {
     if (!h || !o || o->replicas < 1) return 0;
     Plan p;
-    if (make_plan(h, o->replicas, h->force_wpr, h->force_pk, &p) != PDIT_OK) return 0;
+    if (make_plan(h, o->replicas, h->force_wpr, h->force_pk, &p, 0, o->mode == PDIT_MODE_CUPIM) != PDIT_OK) return 0;
     return carve(h, o, p, nullptr).bytes;
 }
 
@@ -457,7 +461,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     int rc = validate_opts(h, o);
     if (rc) return rc;
     Plan plan;
-    rc = make_plan(h, o->replicas, h->force_wpr, h->force_pk, &plan);
+    rc = make_plan(h, o->replicas, h->force_wpr, h->force_pk, &plan, 0, o->mode == PDIT_MODE_CUPIM);
     if (rc) return rc;
     const size_t need = carve(h, o, plan, nullptr).bytes;
     char *base = (char *)o->workspace;
@@ -522,6 +526,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.df_bytes = plan.df_bytes;
     a.group_bytes = plan.group_bytes;
     a.sv_len = plan.sv_len;
+    a.cupim_off = plan.cupim_off;
     a.groups = plan.groups;
     a.target = o->target;
     a.reach_ns = (unsigned long long *)o->reach_ns;

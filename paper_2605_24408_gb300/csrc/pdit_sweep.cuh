@@ -42,7 +42,9 @@ struct SweepArgs {
     uint32_t key0, key1;   // Philox key = seed
     uint32_t inst;         // Philox counter word 0
     uint32_t rep_base;     // global id of local replica 0 (counter word 1)
-    int mode;              // 0 anneal (beta[s]), 1 parallel tempering (beta[rung]), 2 fixed (beta[r])
+    int mode;              // 0 anneal (beta[s]), 1 parallel tempering (beta[rung]), 2 fixed (beta[r]),
+                           // 3 concurrent updates (beta[s])
+    int cupim_off;         // mode 3: offset (int32 entries) of the proposal arrays in the scratch vector
     const float *beta;
     int fresh;             // start from a Fisher-Yates permutation
     int table_in;          // take the influence table from `tables` instead of rebuilding it
@@ -79,8 +81,9 @@ struct GroupScratch {
     int sel_j, sel_d;
     int item;
     int stop;
+    int cnt, aux0, aux1, aux2;
 };
-constexpr size_t kScratchBytes = sizeof(GroupScratch);  // 112
+constexpr size_t kScratchBytes = sizeof(GroupScratch);  // 128
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10, from its published definition (Salmon, Moraes, Dror and
@@ -363,6 +366,99 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
         }
     };
 
+    // Apply the swap i <-> js (facilities fa, fb) to the table (immediately
+    // or as a pending packed term), the p-diagonal and the permutation.
+    // tib, tja: the current I[i][fb], I[js][fa] (thread 0's values are used).
+    // Group-uniform; no barrier at the end.
+    auto apply_swap = [&](int i, int js, int fa, int fb, int tib, int tja) {
+        const DT *Di = sD + i * n;
+        const DT *Dj = sD + js * n;
+        const DT *Fa = sF + fa * n;
+        const DT *Fb = sF + fb * n;
+        if constexpr (PK == 1) {
+            // Immediate rank-1 update: lane l of every warp owns rows
+            // l + 32 k; warp w owns column quads w, w + WPR, ...
+            for (int c = t; c < npad; c += G) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
+            int u[ROWS];
+#pragma unroll
+            for (int k = 0; k < ROWS; ++k) {
+                const int m = lane + 32 * k;
+                u[k] = m < n ? (int)Di[m] - (int)Dj[m] : 0;
+            }
+            group_sync<WPR>(bar);
+            const int4 *v4 = reinterpret_cast<const int4 *>(sv);
+            int cq = wg;
+            for (; cq + (QB - 1) * WPR < nq; cq += QB * WPR) {
+                int4 vq[QB];
+#pragma unroll
+                for (int b = 0; b < QB; ++b) vq[b] = v4[cq + b * WPR];
+                int4 x[ROWS][QB];
+#pragma unroll
+                for (int k = 0; k < ROWS; ++k) {
+                    if (lane + 32 * k < n) {
+                        const int4 *row = reinterpret_cast<const int4 *>(T + (lane + 32 * k) * S) + cq;
+#pragma unroll
+                        for (int b = 0; b < QB; ++b) x[k][b] = row[b * WPR];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < ROWS; ++k) {
+                    if (lane + 32 * k < n) {
+                        int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+#pragma unroll
+                        for (int b = 0; b < QB; ++b) {
+                            add_scaled(x[k][b], u[k], vq[b]);
+                            row[b * WPR] = x[k][b];
+                        }
+                    }
+                }
+            }
+            for (; cq < nq; cq += WPR) {
+                const int4 vq = v4[cq];
+#pragma unroll
+                for (int k = 0; k < ROWS; ++k) {
+                    if (lane + 32 * k < n) {
+                        int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+                        int4 x = *row;
+                        add_scaled(x, u[k], vq);
+                        *row = x;
+                    }
+                }
+            }
+        } else {
+            // Deferred: record u and v of this swap in byte np of upk, vpk.
+            int8_t *ub = reinterpret_cast<int8_t *>(upk) + np;
+            int8_t *vb = reinterpret_cast<int8_t *>(vpk) + np;
+            for (int c = t; c < npad; c += G) {
+                ub[4 * c] = (int8_t)(c < n ? (int)Di[c] - (int)Dj[c] : 0);
+                vb[4 * c] = (int8_t)(c < n ? (int)Fb[c] - (int)Fa[c] : 0);
+            }
+        }
+        // p-diagonal h[m] = I[m][p(m)] under the new influence and
+        // permutation: h[m] += u_m v[p(m)] where p(m) is unchanged;
+        // the two moved entries from the current I[i][fb], I[js][fa].
+        // Thread 0 writes sp[i], sp[js]; those two are not read here.
+        for (int m = t; m < n; m += G)
+            if (m != i && m != js) {
+                const int pm = sp[m];
+                sh[m] += ((int)Di[m] - (int)Dj[m]) * ((int)Fb[pm] - (int)Fa[pm]);
+            }
+        if (t == 0) {
+            sp[i] = fb;
+            sp[js] = fa;
+            sh[i] = tib + ((int)Di[i] - (int)Dj[i]) * ((int)Fb[fb] - (int)Fa[fb]);
+            sh[js] = tja + ((int)Di[js] - (int)Dj[js]) * ((int)Fb[fa] - (int)Fa[fa]);
+        }
+        if constexpr (PK > 1) {
+            ++np;
+            if (np == PK) {
+                group_sync<WPR>(bar);  // packed factors and thread 0's table reads complete
+                flush();
+                np = 0;
+            }
+        }
+    };
+
     for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
         if (a.stop) {
             // group-uniform decision from one read of the instance's flag
@@ -372,7 +468,177 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             group_sync<WPR>(bar);
             if (stop_now) break;
         }
-        const float beta = a.mode != 0 ? beta_fixed : a.beta[s];
+        const float beta = (a.mode == 1 || a.mode == 2) ? beta_fixed : a.beta[s];
+        if (a.mode == 3) {
+            // ---- concurrent updates (one iteration): proposals drawn from a
+            // snapshot of the swap energies, ranked by energy change (ties to
+            // the lower location), greedily accepted when both locations are
+            // free, applied in that order with their exact energy changes.
+            int32_t *pj = sv + a.cupim_off;  // proposal of each location
+            int32_t *pd = pj + npad;          // its snapshot energy change; later: taken flags
+            int32_t *ord = pd + npad;         // movers in priority order; then the accepted ones
+            const uint32_t pmask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
+            // A. warp wg draws the proposals of locations wg, wg + WPR, ...
+            for (int ib = wg; ib < n; ib += 32 * WPR) {
+                const int myrow = ib + WPR * lane;
+                const uint4 rw = philox4x32_10(a.inst, grep, (uint32_t)s, (uint32_t)myrow, a.key0, a.key1);
+                const int nrows = min(32, (n - ib + WPR - 1) / WPR);
+                for (int q = 0; q < nrows; ++q) {
+                    const int i = ib + WPR * q;
+                    const unsigned long long draw =
+                        ((unsigned long long)__shfl_sync(kFull, rw.y, q) << 32) |
+                        (unsigned long long)__shfl_sync(kFull, rw.x, q);
+                    const int fa = sp[i];
+                    const int hi = sh[i];
+                    const DT *Di = sD + i * n;
+                    const DT *Fa = sF + fa * n;
+                    int ui4 = 0, vfa4 = 0;
+                    if constexpr (PK > 1) {
+                        ui4 = (int)(upk[i] & pmask);
+                        vfa4 = (int)vpk[fa];
+                    }
+                    int dv[ROWS];
+                    int lmin = 0x7FFFFFFF;
+#pragma unroll
+                    for (int k = 0; k < ROWS; ++k) {
+                        const int j = lane + 32 * k;
+                        int d = 0x7FFFFFFF;
+                        if (j < n) {
+                            const int b = sp[j];
+                            const int dij = Di[j];
+                            const int fab = Fa[b];
+                            int row_ib = T[i * S + b];
+                            int col_ja = T[j * S + fa];
+                            if constexpr (PK > 1) {
+                                row_ib = __dp4a(ui4, (int)vpk[b], row_ib);
+                                col_ja = __dp4a((int)(upk[j] & pmask), vfa4, col_ja);
+                            }
+                            d = 2 * (row_ib - hi + col_ja - sh[j]);
+                            if (zero_diag)
+                                d += 4 * dij * fab;
+                            else
+                                d += ((int)Di[i] + (int)sD[j * n + j] - 2 * dij) *
+                                     ((int)Fa[fa] + (int)sF[b * n + b] - 2 * fab);
+                            if (j == i) d = 0;
+                            lmin = min(lmin, d);
+                        }
+                        dv[k] = d;
+                    }
+                    const int dmin = __reduce_min_sync(kFull, lmin);
+                    unsigned long long incl[ROWS], tot[ROWS];
+#pragma unroll
+                    for (int k = 0; k < ROWS; ++k)
+                        incl[k] = (lane + 32 * k < n) ? eq5_weight(dv[k] - dmin, beta) : 0ull;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                        for (int k = 0; k < ROWS; ++k) {
+                            const unsigned long long y = __shfl_up_sync(kFull, incl[k], o);
+                            if (lane >= o) incl[k] += y;
+                        }
+                    }
+                    unsigned long long total = 0;
+#pragma unroll
+                    for (int k = 0; k < ROWS; ++k) {
+                        tot[k] = __shfl_sync(kFull, incl[k], 31);
+                        total += tot[k];
+                    }
+                    const unsigned long long tdraw = __umul64hi(draw, total);
+                    int js = i, dsel = 0;
+                    unsigned long long off = 0;
+                    bool found = false;
+#pragma unroll
+                    for (int k = 0; k < ROWS; ++k) {
+                        if (!found && tdraw < off + tot[k]) {  // uniform across the warp
+                            const unsigned ball = __ballot_sync(kFull, off + incl[k] > tdraw);
+                            const int src = __ffs(ball) - 1;
+                            js = 32 * k + src;
+                            dsel = __shfl_sync(kFull, dv[k], src);
+                            found = true;
+                        }
+                        off += tot[k];
+                    }
+                    if (lane == 0) {
+                        pj[i] = js;
+                        pd[i] = dsel;
+                    }
+                }
+            }
+            group_sync<WPR>(bar);
+            // B. priority rank of every mover
+            for (int m = t; m < n; m += G) {
+                const int jm = pj[m];
+                if (jm != m) {
+                    const int dm = pd[m];
+                    int rank = 0;
+                    for (int x = 0; x < n; ++x) {
+                        const int jx = pj[x], dx = pd[x];
+                        rank += (jx != x) && (dx < dm || (dx == dm && x < m));
+                    }
+                    ord[rank] = m;
+                }
+            }
+            group_sync<WPR>(bar);
+            // C. greedy matching in priority order (one thread)
+            if (t == 0) {
+                int movers = 0;
+                for (int x = 0; x < n; ++x) movers += pj[x] != x;
+                for (int x = 0; x < n; ++x) pd[x] = 0;
+                int K = 0;
+                for (int q = 0; q < movers; ++q) {
+                    const int i = ord[q], j = pj[i];
+                    if (!pd[i] && !pd[j]) {
+                        pd[i] = 1;
+                        pd[j] = 1;
+                        ord[K++] = i;
+                    }
+                }
+                gs->cnt = K;
+            }
+            group_sync<WPR>(bar);
+            const int K = gs->cnt;
+            // D. apply the accepted swaps in order, each with its exact energy change
+            for (int q = 0; q < K; ++q) {
+                const int i = ord[q];
+                const int js = pj[i];
+                const int fa = sp[i], fb = sp[js];
+                if (t == 0) {
+                    const uint32_t m4 = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
+                    int rowv = T[i * S + fb];
+                    int colv = T[js * S + fa];
+                    if constexpr (PK > 1) {
+                        rowv = __dp4a((int)(upk[i] & m4), (int)vpk[fb], rowv);
+                        colv = __dp4a((int)(upk[js] & m4), (int)vpk[fa], colv);
+                    }
+                    const int dij = sD[i * n + js];
+                    const int fab = sF[fa * n + fb];
+                    int d = 2 * (rowv - sh[i] + colv - sh[js]);
+                    if (zero_diag)
+                        d += 4 * dij * fab;
+                    else
+                        d += ((int)sD[i * n + i] + (int)sD[js * n + js] - 2 * dij) *
+                             ((int)sF[fa * n + fa] + (int)sF[fb * n + fb] - 2 * fab);
+                    gs->sel_d = d;
+                    gs->aux0 = rowv;
+                    gs->aux1 = colv;
+                }
+                group_sync<WPR>(bar);
+                const int dstar = gs->sel_d;
+                apply_swap(i, js, fa, fb, gs->aux0, gs->aux1);
+                E += dstar;
+                acc_moves += 1;
+                group_sync<WPR>(bar);
+            }
+            // E. best-so-far after the iteration
+            if (E < bestE) {
+                bestE = E;
+                bsweep = s;
+                for (int m = t; m < n; m += G) gbp[m] = sp[m];
+                if (t == 0) note_target(a, bestE, s, reached);
+            }
+            group_sync<WPR>(bar);
+            continue;
+        }
         for (int i0 = 0; i0 < n; i0 += 32) {
             // Philox(inst, replica, sweep, location) for the next 32 locations.
             const uint4 rw = philox4x32_10(a.inst, grep, (uint32_t)s, (uint32_t)(i0 + lane), a.key0, a.key1);
@@ -494,8 +760,6 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
 
                 // ---- apply the swap i <-> js
                 const int fb = sp[js];
-                const DT *Fb = sF + fb * n;
-                const DT *Dj = sD + js * n;
                 // current I[i][fb] and I[js][fa], for the two p-diagonal entries that move
                 int tib = 0, tja = 0;
                 if (t == 0) {
@@ -506,88 +770,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         tja = __dp4a((int)(upk[js] & pmask), vfa4, tja);
                     }
                 }
-                if constexpr (PK == 1) {
-                    // Immediate rank-1 update: lane l of every warp owns rows
-                    // l + 32 k; warp w owns column quads w, w + WPR, ...
-                    for (int c = t; c < npad; c += G) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
-                    int u[ROWS];
-#pragma unroll
-                    for (int k = 0; k < ROWS; ++k) {
-                        const int m = lane + 32 * k;
-                        u[k] = m < n ? (int)Di[m] - (int)Dj[m] : 0;
-                    }
-                    group_sync<WPR>(bar);
-                    const int4 *v4 = reinterpret_cast<const int4 *>(sv);
-                    int cq = wg;
-                    for (; cq + (QB - 1) * WPR < nq; cq += QB * WPR) {
-                        int4 vq[QB];
-#pragma unroll
-                        for (int b = 0; b < QB; ++b) vq[b] = v4[cq + b * WPR];
-                        int4 x[ROWS][QB];
-#pragma unroll
-                        for (int k = 0; k < ROWS; ++k) {
-                            if (lane + 32 * k < n) {
-                                const int4 *row = reinterpret_cast<const int4 *>(T + (lane + 32 * k) * S) + cq;
-#pragma unroll
-                                for (int b = 0; b < QB; ++b) x[k][b] = row[b * WPR];
-                            }
-                        }
-#pragma unroll
-                        for (int k = 0; k < ROWS; ++k) {
-                            if (lane + 32 * k < n) {
-                                int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
-#pragma unroll
-                                for (int b = 0; b < QB; ++b) {
-                                    add_scaled(x[k][b], u[k], vq[b]);
-                                    row[b * WPR] = x[k][b];
-                                }
-                            }
-                        }
-                    }
-                    for (; cq < nq; cq += WPR) {
-                        const int4 vq = v4[cq];
-#pragma unroll
-                        for (int k = 0; k < ROWS; ++k) {
-                            if (lane + 32 * k < n) {
-                                int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
-                                int4 x = *row;
-                                add_scaled(x, u[k], vq);
-                                *row = x;
-                            }
-                        }
-                    }
-                } else {
-                    // Deferred: record u and v of this swap in byte np of upk, vpk.
-                    int8_t *ub = reinterpret_cast<int8_t *>(upk) + np;
-                    int8_t *vb = reinterpret_cast<int8_t *>(vpk) + np;
-                    for (int c = t; c < npad; c += G) {
-                        ub[4 * c] = (int8_t)(c < n ? (int)Di[c] - (int)Dj[c] : 0);
-                        vb[4 * c] = (int8_t)(c < n ? (int)Fb[c] - (int)Fa[c] : 0);
-                    }
-                }
-                // p-diagonal h[m] = I[m][p(m)] under the new influence and
-                // permutation: h[m] += u_m v[p(m)] where p(m) is unchanged;
-                // the two moved entries from the current I[i][fb], I[js][fa].
-                // Thread 0 writes sp[i], sp[js]; those two are not read here.
-                for (int m = t; m < n; m += G)
-                    if (m != i && m != js) {
-                        const int pm = sp[m];
-                        sh[m] += ((int)Di[m] - (int)Dj[m]) * ((int)Fb[pm] - (int)Fa[pm]);
-                    }
-                if (t == 0) {
-                    sp[i] = fb;
-                    sp[js] = fa;
-                    sh[i] = tib + ((int)Di[i] - (int)Dj[i]) * ((int)Fb[fb] - (int)Fa[fb]);
-                    sh[js] = tja + ((int)Di[js] - (int)Dj[js]) * ((int)Fb[fa] - (int)Fa[fa]);
-                }
-                if constexpr (PK > 1) {
-                    ++np;
-                    if (np == PK) {
-                        group_sync<WPR>(bar);  // packed factors and thread 0's table reads complete
-                        flush();
-                        np = 0;
-                    }
-                }
+                apply_swap(i, js, fa, fb, tib, tja);
                 E += dstar;
                 acc_moves += 1;
                 if (E < bestE) {

@@ -29,6 +29,7 @@ PDIT_N_MAX = 256
 PDIT_MODE_ANNEAL = 0
 PDIT_MODE_PT = 1
 PDIT_MODE_FIXED = 2
+PDIT_MODE_CUPIM = 3
 PDIT_FLAG_RESUME = 1
 PDIT_BATCH_STOP_AT_TARGET = 1
 PDIT_BATCH_GRAPH = 2

@@ -295,3 +295,17 @@ def test_beta_range_selection_matches_oracle():
     assert np.array_equal(curve, omean)
     assert lo == olo and hi == ohi
     assert lo <= hi
+
+
+# --- concurrent updates (GPU-CUPIM) -----------------------------------------------
+
+@pytest.mark.parametrize("name,n,wpr,pk", [("n12", 12, 0, 0), ("n30", 30, 0, 0), ("dense", 100, 4, 4),
+                                          ("dense", 100, 2, 1), ("dense", 100, 1, 4), ("dense", 150, 0, 0),
+                                          ("dense", 256, 0, 0)])
+def test_cupim_matches_oracle(name, n, wpr, pk):
+    D, F = G.named(name) if name != "dense" else G.dense_instance(n, seed=n)
+    S = 12
+    beta = schedule(D, F, "linear", S)
+    g = gpu_run(D, F, beta, S, 31, 6, tables=True, wpr=wpr, pk=pk, mode=3)
+    r = O.anneal(D, F, beta, S, 31, 0, 6, mode="cupim", threads=6, tables=True)
+    check_equal(g, r, tables=True)

@@ -423,3 +423,34 @@ def test_beta_range_curve_shape_on_n12():
     assert grid[0] <= lo <= hi <= grid[-1]
     # high temperature: mean ending energy well above the brute-force optimum
     assert mean[0] > 564 and mean.min() >= 564
+
+
+# --- Concurrent updates (GPU-CUPIM Algorithm section) ----------------------------
+
+def test_cupim_invariants_and_matching_bound():
+    D, F = G.named("n30")
+    n = 30
+    S = 40
+    beta = O.beta_schedule("linear", S, O.beta_max(D, F))
+    r = O.anneal(D, F, beta, S, 3, 0, 4, mode="cupim", tables=True)
+    for k in range(4):
+        assert sorted(r["final_perm"][k]) == list(range(n))
+        assert r["final_cost"][k] == O.cost(D, F, r["final_perm"][k])
+        assert r["best_cost"][k] == O.cost(D, F, r["best_perm"][k])
+        assert np.array_equal(r["tables"][k], O.influence(D, F, r["final_perm"][k]))
+        # the accepted swaps of one iteration are disjoint: at most n/2 per iteration
+        assert r["accepted"][k] <= S * (n // 2)
+
+
+def test_cupim_single_mover_equals_sequential_update():
+    """With beta = 0 for all but one location's draw the structure is opaque;
+    instead: on N = 2 there is one possible swap, proposed by both locations in
+    the same iteration only once -> CUPIM applies at most one swap per
+    iteration, and a sequential sweep applies at most two."""
+    D = np.array([[0, 3], [3, 0]], np.int32)
+    F = np.array([[0, 5], [5, 0]], np.int32)
+    beta = np.zeros(20, np.float32)
+    r = O.anneal(D, F, beta, 20, 1, 0, 8, mode="cupim")
+    assert (r["accepted"] <= 20).all()
+    # every permutation of two locations has the same cost
+    assert (r["final_cost"] == 30).all()
