@@ -147,9 +147,10 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     }
     if (wpr <= 0) {
         // Aim for about 16 resident warps per SM to hide the latency of each
-        // replica's sequential update chain.
+        // replica's sequential update chain; tables in global memory are
+        // latency-bound on every access, so they take the most warps.
         wpr = 1;
-        while (wpr < cover / 32 && std::min(fit, 32 / wpr) * wpr < 16) wpr <<= 1;
+        while (wpr < cover / 32 && (!p->tsmem || std::min(fit, 32 / wpr) * wpr < 16)) wpr <<= 1;
     }
     if (wpr < 1 || wpr > cover / 32 || (wpr & (wpr - 1))) return PDIT_EINVAL;
     p->wpr = wpr;

@@ -220,7 +220,7 @@ __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
 // updates lane l of each warp owns rows l + 32 k. PK = pending swaps held
 // before the table is rewritten (1 = immediate rank-1 updates).
 // ---------------------------------------------------------------------------
-template <typename DT, int MAXK, int WPR, int PK>
+template <typename DT, int MAXK, int WPR, int PK, bool TG = false>
 __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, int bar,
                                             const DT *sD, const DT *sF, int32_t *T, int32_t *sp,
                                             int32_t *sh, int32_t *sv, uint32_t *upk,
@@ -228,6 +228,10 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     constexpr int G = 32 * WPR;
     constexpr int ROWS = WPR * MAXK;       // table rows per lane in the rank-1 update (32-row slots)
     constexpr int QB = ROWS <= 4 ? 2 : 1;  // table quads per batch of the rank-1 update
+    // Tables in global memory (TG): table updates run lanes along a row, so a
+    // warp touches 512 contiguous bytes per access; each lane keeps the
+    // column factors of its quads lane, lane + 32, ... in registers.
+    constexpr int QL = (ROWS + 3) / 4;     // quads per lane along a row (cover / 128)
     const int lane = t & 31;
     const int wg = t >> 5;
     const int n = a.n;
@@ -343,6 +347,32 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     // T += sum_{q < np} u_q (x) v_q on this thread's (rows, column quads).
     auto flush = [&]() {
         const uint32_t mask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
+        if constexpr (TG) {
+            int4 vq[QL];
+#pragma unroll
+            for (int c2 = 0; c2 < QL; ++c2) {
+                const int cq = lane + 32 * c2;
+                vq[c2] = cq < nq ? reinterpret_cast<const int4 *>(vpk)[cq] : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll 2
+            for (int m = wg; m < n; m += WPR) {
+                const int um = (int)(upk[m] & mask);
+                int4 *row = reinterpret_cast<int4 *>(T + m * S);
+#pragma unroll
+                for (int c2 = 0; c2 < QL; ++c2) {
+                    const int cq = lane + 32 * c2;
+                    if (cq < nq) {
+                        int4 x = row[cq];
+                        x.x = __dp4a(um, vq[c2].x, x.x);
+                        x.y = __dp4a(um, vq[c2].y, x.y);
+                        x.z = __dp4a(um, vq[c2].z, x.z);
+                        x.w = __dp4a(um, vq[c2].w, x.w);
+                        row[cq] = x;
+                    }
+                }
+            }
+            return;
+        }
         int uw[ROWS];
 #pragma unroll
         for (int k = 0; k < ROWS; ++k) {
@@ -379,6 +409,29 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             // Immediate rank-1 update: lane l of every warp owns rows
             // l + 32 k; warp w owns column quads w, w + WPR, ...
             for (int c = t; c < npad; c += G) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
+            if constexpr (TG) {
+                group_sync<WPR>(bar);
+                int4 vq[QL];
+#pragma unroll
+                for (int c2 = 0; c2 < QL; ++c2) {
+                    const int cq = lane + 32 * c2;
+                    vq[c2] = cq < nq ? reinterpret_cast<const int4 *>(sv)[cq] : make_int4(0, 0, 0, 0);
+                }
+#pragma unroll 2
+                for (int m = wg; m < n; m += WPR) {
+                    const int um = (int)Di[m] - (int)Dj[m];
+                    int4 *row = reinterpret_cast<int4 *>(T + m * S);
+#pragma unroll
+                    for (int c2 = 0; c2 < QL; ++c2) {
+                        const int cq = lane + 32 * c2;
+                        if (cq < nq) {
+                            int4 x = row[cq];
+                            add_scaled(x, um, vq[c2]);
+                            row[cq] = x;
+                        }
+                    }
+                }
+            } else {
             int u[ROWS];
 #pragma unroll
             for (int k = 0; k < ROWS; ++k) {
@@ -424,6 +477,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         *row = x;
                     }
                 }
+            }
             }
         } else {
             // Deferred: record u and v of this swap in byte np of upk, vpk.
@@ -859,10 +913,10 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(
         const int item = gs->item;
         if (item >= a.replicas) break;
         if constexpr (TSMEM) {
-            run_replica<DT, MAXK, WPR, PK>(a, item, t, bar, sD, sF, sT, sp, sh, sv, upk, vpk, gs);
+            run_replica<DT, MAXK, WPR, PK, false>(a, item, t, bar, sD, sF, sT, sp, sh, sv, upk, vpk, gs);
         } else {
-            run_replica<DT, MAXK, WPR, PK>(a, item, t, bar, sD, sF,
-                                           a.tables + (size_t)item * n * a.stride, sp, sh, sv, upk, vpk, gs);
+            run_replica<DT, MAXK, WPR, PK, true>(a, item, t, bar, sD, sF,
+                                                 a.tables + (size_t)item * n * a.stride, sp, sh, sv, upk, vpk, gs);
         }
     }
 }
@@ -927,7 +981,7 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
             uint32_t *upk = reinterpret_cast<uint32_t *>(sv + sa.sv_len);
             uint32_t *vpk = upk + npad;
             int32_t *T = TSMEM ? sT : sa.tables + (size_t)r * n * sa.stride;
-            run_replica<DT, MAXK, WPR, PK>(sa, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
+            run_replica<DT, MAXK, WPR, PK, !TSMEM>(sa, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
         }
     }
 }
