@@ -42,7 +42,7 @@ class _Replica(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int),
                 ("D", ctypes.c_void_p), ("F", ctypes.c_void_p),
                 ("p", ctypes.c_void_p), ("I", ctypes.c_void_p),
-                ("E", ctypes.c_int64)]
+                ("E", ctypes.c_int64), ("general", ctypes.c_int)]
 
 
 def lib():
@@ -64,6 +64,10 @@ def lib():
         L.oracle_influence_eq2.restype = None
         L.oracle_delta_e.argtypes = [c_int, I32P, I32P, I32P, I64P, c_int, c_int]
         L.oracle_delta_e.restype = c_i64
+        L.oracle_delta_e_eq3.argtypes = [c_int, I32P, I32P, I32P, I64P, c_int, c_int]
+        L.oracle_delta_e_eq3.restype = c_i64
+        L.oracle_is_symmetric.argtypes = [c_int, I32P]
+        L.oracle_is_symmetric.restype = c_int
         L.oracle_expneg_f32.argtypes = [ctypes.c_float]
         L.oracle_expneg_f32.restype = ctypes.c_float
         L.oracle_weight.argtypes = [ctypes.c_float]
@@ -75,7 +79,7 @@ def lib():
         L.oracle_anneal.argtypes = [c_int, I32P, I32P, c_int, c_int, c_int, c_int, c_int, c_int,
                                     F32P, c_int, c_u64, c_u32, c_int,
                                     I32P, I64P, I32P, I64P, I32P, I64P, vp, vp, vp,
-                                    c_int, c_i64, vp]
+                                    c_int, c_i64, vp, c_int]
         L.oracle_anneal.restype = c_int
         L.oracle_argmin_best.argtypes = [c_int, I64P]
         L.oracle_argmin_best.restype = c_int
@@ -139,6 +143,23 @@ def delta_e(D, F, p, I, i: int, j: int) -> int:
                                     np.ascontiguousarray(I, dtype=np.int64), i, j))
 
 
+def delta_e_eq3(D, F, p, Ip, i: int, j: int) -> int:
+    """Eq. 3 as printed, with Eq. 2's table Ip (general D and F)."""
+    D, F = _i32(D), _i32(F)
+    return int(lib().oracle_delta_e_eq3(D.shape[0], D, F, _i32(p),
+                                        np.ascontiguousarray(Ip, dtype=np.int64), i, j))
+
+
+def is_symmetric(M) -> bool:
+    M = _i32(M)
+    return bool(lib().oracle_is_symmetric(M.shape[0], M))
+
+
+def general_form(D, F) -> bool:
+    """True when the oracle runs the general form for (D, F)."""
+    return not (is_symmetric(D) and is_symmetric(F))
+
+
 def expneg_f32(x: float) -> np.float32:
     return np.float32(lib().oracle_expneg_f32(float(np.float32(x))))
 
@@ -147,16 +168,19 @@ def weight(x: float) -> int:
     return int(lib().oracle_weight(float(np.float32(x))))
 
 
-def choose(D, F, p, i: int, beta: float, r: int):
+def choose(D, F, p, i: int, beta: float, r: int, general: bool | None = None):
     """One Eq. 5 update at location i from state p (table built from p).
     Returns (chosen j, dE[n] int64, weights[n] uint64, near-boundary flag)."""
     D, F, p = _i32(D), _i32(F), _i32(p).copy()
     n = D.shape[0]
-    I = influence(D, F, p)
+    if general is None:
+        general = general_form(D, F)
+    I = influence_eq2(D, F, p) if general else influence(D, F, p)
     dE = np.zeros(n, dtype=np.int64)
     w = np.zeros(n, dtype=np.uint64)
     near = ctypes.c_int(0)
-    rep = _Replica(n, D.ctypes.data, F.ctypes.data, p.ctypes.data, I.ctypes.data, cost(D, F, p))
+    rep = _Replica(n, D.ctypes.data, F.ctypes.data, p.ctypes.data, I.ctypes.data, cost(D, F, p),
+                   1 if general else 0)
     j = lib().oracle_choose(ctypes.byref(rep), i, float(np.float32(beta)), r & 0xFFFFFFFFFFFFFFFF,
                             dE.ctypes.data, w.ctypes.data, ctypes.addressof(near))
     return j, dE, w, near.value
@@ -196,12 +220,15 @@ def beta_schedule(kind: str, sweeps: int, bmax: float) -> np.ndarray:
 def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int = 1,
            inst: int = 0, threads: int = 1, mode: str = "anneal", ladder_len: int = 0,
            period: int = 4, timeout: int = 100, near: bool = False, tables: bool = False,
-           target=None) -> dict:
+           target=None, form: str = "auto") -> dict:
     """Runs replicas [rep_begin, rep_end). mode 'anneal': beta[s] per sweep;
     mode 'pt': beta is the ladder (rung 0 = smallest beta), sets of ladder_len
     consecutive replicas exchange every `period` sweeps; mode 'fixed':
     beta[k] for the k-th replica of the call, no exchange; mode 'cupim':
-    concurrent updates, beta[s] per iteration."""
+    concurrent updates, beta[s] per iteration. form 'auto': the symmetric
+    form (table I) when D and F are symmetric, else the general form (Eq. 2's
+    table Ip, Eq. 3 as printed); 'general': the general form always.
+    out['tables'] holds the table of the form used; out['general'] says which."""
     D, F = _i32(D), _i32(F)
     n = D.shape[0]
     R = rep_end - rep_begin
@@ -221,7 +248,9 @@ def anneal(D, F, beta, sweeps: int, seed: int, rep_begin: int = 0, rep_end: int 
         tab.ctypes.data if tab is not None else None,
         rung.ctypes.data if rung is not None else None,
         1 if target is not None else 0, int(target) if target is not None else 0,
-        reach.ctypes.data if reach is not None else None)
+        reach.ctypes.data if reach is not None else None,
+        {"auto": 0, "general": 1}[form])
+    out["general"] = form == "general" or general_form(D, F)
     if rc != 0:
         raise ValueError("oracle_anneal rejected its arguments")
     if nb is not None:

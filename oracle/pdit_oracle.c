@@ -1,5 +1,6 @@
 /*
- * CPU ORACLE for the annealed p-dit sweep on the symmetric QAP.
+ * CPU ORACLE for the annealed p-dit sweep on the QAP (symmetric, and the
+ * general form with asymmetric D, F or nonzero diagonals).
  *
  * TEST INFRASTRUCTURE, NOT PRODUCT CODE. Only tests/, __graft_entry__.smoke()
  * and the CPU-baseline / reference arm of bench.py load this library. It
@@ -17,6 +18,9 @@
  *                         the paper's I equals -2 times this (reading R1).
  *   oracle_delta_e        Eq. 3 restated in those units (reading R2: Eq. 3,
  *                         not the Eq. 4 shortcut, which drops a term).
+ *   oracle_delta_e_eq3    the general form: Eq. 2 taken literally (both
+ *                         terms, the paper's sign) and Eq. 3 taken literally;
+ *                         used when D or F is not symmetric (reading R13).
  *   oracle_update         Eq. 5 over the N outcomes of one p-dit update
  *                         (swap with each other location, or stay), sampled
  *                         with the fp32 weights of reading R4.
@@ -44,7 +48,10 @@
  * double Eq. 5, beta = 0 (uniform) and beta -> infinity (argmin) closed
  * forms, and a chi-square test of the one-step law; anneal results against
  * brute-force optima for N <= 9; parallel-tempering exchange on hand-made
- * energy sequences.
+ * energy sequences. General form (tests/test_oracle_general.py): Eq. 1 on a
+ * hand-worked asymmetric case, Eq. 3 as printed against brute recomputation
+ * with any diagonal, sum_m Ip[m][p(m)] = -2 E, and the exact reduction of a
+ * one-sided asymmetric instance to the symmetric form at half the beta.
  *
  * Floating point: compile with -ffp-contract=off; every float operation below
  * is one correctly rounded IEEE binary32 operation (fmaf is a fused one).
@@ -187,6 +194,50 @@ static void apply_swap_to_influence(int n, const int32_t *D, const int32_t *F, i
         }
 }
 
+/* General D and F (reading R13). Eq. 3 with the table Ip of Eq. 2 as printed:
+ *   dE = -[Ip_ib - Ip_ia + Ip_ja - Ip_jb - (D_ii + D_jj - D_ij - D_ji)(F_aa + F_bb - F_ab - F_ba)]
+ * with a = p(i), b = p(j); staying (j == i) changes nothing. */
+int64_t oracle_delta_e_eq3(int n, const int32_t *D, const int32_t *F, const int32_t *p,
+                           const int64_t *Ip, int i, int j) {
+    if (i == j) return 0;
+    int a = p[i], b = p[j];
+    int64_t t = Ip[(size_t)i * n + b] - Ip[(size_t)i * n + a] + Ip[(size_t)j * n + a] -
+                Ip[(size_t)j * n + b];
+    int64_t dd = (int64_t)D[(size_t)i * n + i] + D[(size_t)j * n + j] - D[(size_t)i * n + j] -
+                 D[(size_t)j * n + i];
+    int64_t ff = (int64_t)F[(size_t)a * n + a] + F[(size_t)b * n + b] - F[(size_t)a * n + b] -
+                 F[(size_t)b * n + a];
+    return -(t - dd * ff);
+}
+
+/* Eq. 2's table after the swap (facility a at i moves to j, b at j moves to
+ * i). Of the sum over j in Eq. 2 only the terms of locations i and j change:
+ *   Ip[m][c] -= D[m][i] (F[c][b] - F[c][a]) + D[m][j] (F[c][a] - F[c][b])
+ *             + D[i][m] (F[b][c] - F[a][c]) + D[j][m] (F[a][c] - F[b][c]). */
+static void apply_swap_to_eq2(int n, const int32_t *D, const int32_t *F, int64_t *Ip, int i,
+                              int j, int a, int b) {
+    for (int m = 0; m < n; ++m)
+        for (int c = 0; c < n; ++c) {
+            int64_t out_i = (int64_t)D[(size_t)m * n + i] *
+                            ((int64_t)F[(size_t)c * n + b] - F[(size_t)c * n + a]);
+            int64_t out_j = (int64_t)D[(size_t)m * n + j] *
+                            ((int64_t)F[(size_t)c * n + a] - F[(size_t)c * n + b]);
+            int64_t in_i = (int64_t)D[(size_t)i * n + m] *
+                           ((int64_t)F[(size_t)b * n + c] - F[(size_t)a * n + c]);
+            int64_t in_j = (int64_t)D[(size_t)j * n + m] *
+                           ((int64_t)F[(size_t)a * n + c] - F[(size_t)b * n + c]);
+            Ip[(size_t)m * n + c] -= out_i + out_j + in_i + in_j;
+        }
+}
+
+/* 1 if M equals its transpose. */
+int oracle_is_symmetric(int n, const int32_t *M) {
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (M[(size_t)i * n + j] != M[(size_t)j * n + i]) return 0;
+    return 1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Reading R4: the Eq. 5 weights in binary32.                               */
 /*   x = (float)(dE_j - dE_min) * beta                  (one rounded multiply)
@@ -235,8 +286,9 @@ typedef struct {
     int n;
     const int32_t *D, *F;
     int32_t *p;
-    int64_t *I;
+    int64_t *I;     /* symmetric form: I of reading R1; general form: Ip of Eq. 2 */
     int64_t E;
+    int general;    /* 1: the general form (reading R13) */
 } replica_t;
 
 /* Exact double-precision Eq. 5 CDF boundaries, used only to count the draws
@@ -269,7 +321,9 @@ int oracle_choose(const replica_t *R, int i, float beta, uint64_t r, int64_t *dE
     int n = R->n;
     int64_t *dE = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
-    for (int j = 0; j < n; ++j) dE[j] = oracle_delta_e(n, R->D, R->F, R->p, R->I, i, j);
+    for (int j = 0; j < n; ++j)
+        dE[j] = R->general ? oracle_delta_e_eq3(n, R->D, R->F, R->p, R->I, i, j)
+                           : oracle_delta_e(n, R->D, R->F, R->p, R->I, i, j);
     int64_t dmin = dE[0];
     for (int j = 1; j < n; ++j)
         if (dE[j] < dmin) dmin = dE[j];
@@ -300,7 +354,10 @@ int oracle_choose(const replica_t *R, int i, float beta, uint64_t r, int64_t *dE
 /* Apply the chosen swap: influence table, permutation, energy. */
 static void apply_choice(replica_t *R, int i, int j, int64_t dEj) {
     int a = R->p[i], b = R->p[j];
-    apply_swap_to_influence(R->n, R->D, R->F, R->I, i, j, a, b);
+    if (R->general)
+        apply_swap_to_eq2(R->n, R->D, R->F, R->I, i, j, a, b);
+    else
+        apply_swap_to_influence(R->n, R->D, R->F, R->I, i, j, a, b);
     R->p[i] = b;
     R->p[j] = a;
     R->E += dEj;
@@ -368,6 +425,7 @@ typedef struct {
     int has_target;       /* record the first sweep at which best <= target */
     int64_t target;
     int32_t *reach;       /* [R] or NULL: that sweep (-1 = initial state), INT32_MAX if never */
+    int general;          /* keep Eq. 2's table and use Eq. 3 as printed (reading R13) */
     int status;
 } anneal_job_t;
 
@@ -425,7 +483,8 @@ static int cupim_iteration(replica_t *X, float beta, uint64_t seed, uint32_t ins
         int i = prop[a].i, j = prop[a].j;
         if (taken[i] || taken[j]) continue;
         taken[i] = taken[j] = 1;
-        int64_t d = oracle_delta_e(n, X->D, X->F, X->p, X->I, i, j);
+        int64_t d = X->general ? oracle_delta_e_eq3(n, X->D, X->F, X->p, X->I, i, j)
+                               : oracle_delta_e(n, X->D, X->F, X->p, X->I, i, j);
         apply_choice(X, i, j, d);
         ++applied;
     }
@@ -450,8 +509,12 @@ static void run_job(anneal_job_t *J) {
         X->F = J->F;
         X->p = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
         X->I = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * n);
+        X->general = J->general;
         oracle_init_perm(n, J->seed, J->inst, rep, X->p);
-        oracle_influence(n, J->D, J->F, X->p, X->I);
+        if (X->general)
+            oracle_influence_eq2(n, J->D, J->F, X->p, X->I);
+        else
+            oracle_influence(n, J->D, J->F, X->p, X->I);
         X->E = oracle_cost(n, J->D, J->F, X->p);
         memcpy(J->best_p + (size_t)k * n, X->p, sizeof(int32_t) * (size_t)n);
         J->best_E[k] = X->E;
@@ -531,14 +594,18 @@ static void *job_thread(void *arg) {
 /* Runs replicas [rep_begin, rep_end) on `threads` POSIX threads, each a
  * contiguous block of whole replicas (whole PT sets in PT mode). Every
  * replica is an independent chain, so the split does not change results.
- * Returns 0, or -1 on invalid arguments. */
+ * form: 0 = the symmetric form when D and F are both symmetric, else the
+ * general form; 1 = the general form always. final_I receives the table of
+ * the form used (I, or Eq. 2's Ip). Returns 0, or -1 on invalid arguments. */
 int oracle_anneal(int n, const int32_t *D, const int32_t *F, int rep_begin, int rep_end,
                   int mode, int ladder_len, int period, int timeout, const float *beta,
                   int sweeps, uint64_t seed, uint32_t inst, int threads, int32_t *final_p,
                   int64_t *final_E, int32_t *best_p, int64_t *best_E, int32_t *best_sweep,
                   int64_t *accepted, int64_t *near, int64_t *final_I, int32_t *final_rung,
-                  int has_target, int64_t target, int32_t *reach) {
+                  int has_target, int64_t target, int32_t *reach, int form) {
     if (n < 2 || rep_end <= rep_begin || sweeps < 0 || !D || !F || !beta) return -1;
+    if (form != 0 && form != 1) return -1;
+    const int general = form == 1 || !oracle_is_symmetric(n, D) || !oracle_is_symmetric(n, F);
     int R = rep_end - rep_begin;
     int unit = 1;
     if (mode == 1) {
@@ -581,6 +648,7 @@ int oracle_anneal(int n, const int32_t *D, const int32_t *F, int rep_begin, int 
         J->has_target = has_target;
         J->target = target;
         J->reach = reach ? reach + k0 : NULL;
+        J->general = general;
     }
     if (threads == 1) {
         run_job(&jobs[0]);
@@ -644,19 +712,25 @@ int64_t oracle_brute_force(int n, const int32_t *D, const int32_t *F, int32_t *b
 
 /* ------------------------------------------------------------------------ */
 /* Beta schedules (reading R8). beta_max convention: 10 / mean positive dE   */
-/* over all n(n-1)/2 swaps from the identity permutation, Eq. 3.            */
+/* over all n(n-1)/2 swaps from the identity permutation, Eq. 3 (the general */
+/* form when D or F is not symmetric).                                      */
 /* kind 0: linear 0 -> beta_max; kind 1: geometric beta_max/1000 -> beta_max */
 /* ------------------------------------------------------------------------ */
 double oracle_beta_max(int n, const int32_t *D, const int32_t *F) {
     int32_t *p = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int64_t *I = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * n);
     for (int k = 0; k < n; ++k) p[k] = k;
-    oracle_influence(n, D, F, p, I);
+    const int general = !oracle_is_symmetric(n, D) || !oracle_is_symmetric(n, F);
+    if (general)
+        oracle_influence_eq2(n, D, F, p, I);
+    else
+        oracle_influence(n, D, F, p, I);
     double sum = 0.0;
     int64_t cnt = 0;
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
-            int64_t d = oracle_delta_e(n, D, F, p, I, i, j);
+            int64_t d = general ? oracle_delta_e_eq3(n, D, F, p, I, i, j)
+                                : oracle_delta_e(n, D, F, p, I, i, j);
             if (d > 0) {
                 sum += (double)d;
                 cnt += 1;

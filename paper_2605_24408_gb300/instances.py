@@ -154,6 +154,29 @@ def random_symmetric(n: int, lo: int, hi: int, seed: int, tag: int, diag: bool =
     return m.astype(np.int32)
 
 
+def asymmetric(n: int, lo: int, hi: int, seed: int, tag: int, diag: bool = False) -> np.ndarray:
+    """n x n matrix with every entry drawn independently, uniform in lo..hi (no
+    symmetry); the diagonal is zero unless `diag`."""
+    M = hash_int(seed, tag, np.arange(n * n, dtype=np.uint64), lo, hi).reshape(n, n)
+    if not diag:
+        M[np.arange(n), np.arange(n)] = 0
+    return M.astype(np.int32)
+
+
+def asymmetric_instance(n: int, seed: int, diag: bool = False):
+    """The general-QAP workload: directed distances (grid-Manhattan plus a
+    one-way surcharge 0..9 per ordered pair) and a dense asymmetric flow in
+    0..99; `diag` adds a nonzero diagonal to both."""
+    rows, cols = near_square_grid(n)
+    D = grid_manhattan(rows, cols, n).astype(np.int64) + asymmetric(n, 0, 9, seed, 91)
+    F = asymmetric(n, 0, 99, seed, 95, diag)
+    if diag:
+        D[np.arange(n), np.arange(n)] = hash_int(seed, 93, np.arange(n, dtype=np.uint64), 1, 9)
+    else:
+        D[np.arange(n), np.arange(n)] = 0
+    return D.astype(np.int32), F
+
+
 def request_instance(request_id: int, lo: int = 20, hi: int = 200):
     """The instance of a serving request: N uniform in lo..hi from the request
     id, then the ragged-batch generator keyed by the request id."""
