@@ -1,6 +1,6 @@
 /*
- * libpdit -- p-dit probabilistic Ising machine for the symmetric quadratic
- * assignment problem, on NVIDIA GB300 (sm_103a).
+ * libpdit -- p-dit probabilistic Ising machine for the quadratic assignment
+ * problem, on NVIDIA GB300 (sm_103a).
  *
  * Method: arXiv 2605.24408, "P-dit Probabilistic Ising Machine for Solving
  * the Quadratic Assignment Problem". The QAP is min_p sum_ij D_ij F_{p(i)p(j)}
@@ -12,6 +12,10 @@
  * sweep updates every location once, in index order. Plain mode anneals the
  * inverse temperature beta along a per-sweep schedule; PT mode runs
  * parallel tempering (Implementation section; CPU-PIM Algorithm section).
+ * Symmetric instances keep the one-term table I[m][c] = sum_j D[m][j]
+ * F[c][p(j)] (for them Eq. 2 equals -2 I); instances with a non-symmetric
+ * D or F keep Eq. 2's two-term table and use Eq. 3 as printed, which is
+ * exact for any D and F.
  *
  * Conventions for every call:
  *  - Return 0 (PDIT_OK) on success, a negative PDIT_E* code on failure. No
@@ -38,7 +42,7 @@ extern "C" {
 
 /* ---- error codes ------------------------------------------------------- */
 #define PDIT_OK 0
-#define PDIT_EINVAL (-1)  /* NULL pointer, size out of range, D or F not symmetric, bad beta */
+#define PDIT_EINVAL (-1)  /* NULL pointer, size out of range, bad beta */
 #define PDIT_ERANGE (-2)  /* 16 (N+2) max|D| max|F| >= 2^31: the int32 tables could overflow */
 #define PDIT_ENOMEM (-3)  /* an allocation failed, or the caller's workspace is too small */
 #define PDIT_ECUDA (-4)   /* a CUDA runtime call failed; see pdit_last_error() */
@@ -66,12 +70,12 @@ typedef struct pdit_qap pdit_qap;
  * qap_create -- upload one QAP instance (Eq. 1 inputs) to the current CUDA
  * device.
  *   n      : 2 <= n <= PDIT_N_MAX.
- *   D, F   : host pointers, n*n int32 each, row-major; both must be
- *            symmetric (the paper treats the symmetric QAP, Eq. 1). Any
- *            diagonal and any sign are accepted. Copied; the caller keeps
- *            ownership.
+ *   D, F   : host pointers, n*n int32 each, row-major. Symmetric or not
+ *            (Eq. 2 and Eq. 3 cover the general QAP; the paper's instances
+ *            are symmetric), any diagonal, any sign. Copied; the caller
+ *            keeps ownership.
  *   out    : receives the handle (owns device copies of D and F).
- * Errors: PDIT_EINVAL (n out of range, NULL, asymmetric), PDIT_ERANGE
+ * Errors: PDIT_EINVAL (n out of range, NULL), PDIT_ERANGE
  * (values too large for exact int32 table arithmetic), PDIT_ENOMEM,
  * PDIT_ECUDA. On error *out is set to NULL.
  */
@@ -238,8 +242,9 @@ int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out);
  * other allocating call. The paper has no counterpart; this is a packaging
  * of the same computation.
  *   n, D, F  : instance size and DEVICE pointers to the int32 row-major
- *              matrices, symmetric, 16 (n+2) max|D| max|F| < 2^31 (not
- *              checked here: the values stay on the device).
+ *              matrices, symmetric (the values stay on the device, so
+ *              this entry point cannot detect the general form), 16 (n+2)
+ *              max|D| max|F| < 2^31 (not checked here).
  *   replicas, beta (DEVICE, `sweeps` floats), sweeps, seed: as pdit_anneal.
  *   best_perm (DEVICE, n int32), best_cost (DEVICE, 1 int64): outputs.
  *   stream   : cudaStream_t (NULL = legacy default stream); asynchronous.
@@ -366,7 +371,7 @@ int pdit_server_create(size_t device_budget_bytes, int slice_sweeps, int max_act
 
 /*
  * pdit_server_submit -- queue one request: host D, F (n x n int32,
- * symmetric, copied), replicas, sweeps, seed, request_id (Philox counter
+ * symmetric or not, copied), replicas, sweeps, seed, request_id (Philox counter
  * word 0), and beta (host [sweeps]; NULL = the linear schedule
  * 0 -> pdit_beta_max). Thread-safe. *ticket identifies the request.
  * Errors: PDIT_EINVAL, PDIT_ENOMEM.

@@ -22,6 +22,7 @@ struct pdit_qap {
     size_t l2_bytes = 0;
     int dt_bytes = 4;       // storage of D and F in shared memory: 1, 2 or 4 bytes
     int zero_diag = 0;
+    int asym = 0;           // D or F not symmetric: the general form (two-term table)
     int packed_ok = 0;      // max-min of D and of F <= 127: swap factors fit int8
     std::vector<int32_t> hD, hF;
     int32_t *dD = nullptr, *dF = nullptr;
@@ -71,28 +72,50 @@ int cover_for(int n) {
     return c;
 }
 
+// Row stride (elements) of D and F as staged for the general form: rows of
+// 4 x odd bytes, so that the 32 lanes of a warp reading one column hit 32
+// distinct banks.
+int stage_stride(int n, int dt) {
+    const int per_word = 4 / dt;
+    int words = (n + per_word - 1) / per_word;
+    if (words % 2 == 0) words += 1;
+    return words * per_word;
+}
+
 struct Plan {
     int maxk = 1, wpr = 1, pk = 1;
     bool tsmem = true;
-    int stride = 0, sv_len = 0, cupim_off = 0;
+    int stride = 0, sv_len = 0, cupim_off = 0, v2_off = 0, dstride = 0;
     size_t df_bytes = 0, group_bytes = 0, smem = 0;
     int groups = 1, threads = 32, grid = 1;
 };
 
 
-int sweep_blocks(int dt, const Plan &p, int *blocks) {
-    if (dt == 1) return pdit::sweep_blocks_per_sm<int8_t>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
-    if (dt == 2) return pdit::sweep_blocks_per_sm<int16_t>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
-    return pdit::sweep_blocks_per_sm<int32_t>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
+template <bool ASYM>
+int sweep_blocks_t(int dt, const Plan &p, int *blocks) {
+    if (dt == 1) return pdit::sweep_blocks_per_sm<int8_t, ASYM>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
+    if (dt == 2) return pdit::sweep_blocks_per_sm<int16_t, ASYM>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
+    return pdit::sweep_blocks_per_sm<int32_t, ASYM>(p.maxk, p.wpr, p.tsmem, p.pk, p.threads, p.smem, blocks);
 }
 
-int sweep_launch(int dt, const Plan &p, const pdit::SweepArgs &a, cudaStream_t st) {
-    if (dt == 1) return pdit::sweep_launch<int8_t>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
-    if (dt == 2) return pdit::sweep_launch<int16_t>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
-    return pdit::sweep_launch<int32_t>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
+int sweep_blocks(int dt, bool asym, const Plan &p, int *blocks) {
+    return asym ? sweep_blocks_t<true>(dt, p, blocks) : sweep_blocks_t<false>(dt, p, blocks);
 }
 
-// Scratch-vector length (int32 entries) of a group.
+template <bool ASYM>
+int sweep_launch_t(int dt, const Plan &p, const pdit::SweepArgs &a, cudaStream_t st) {
+    if (dt == 1) return pdit::sweep_launch<int8_t, ASYM>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
+    if (dt == 2) return pdit::sweep_launch<int16_t, ASYM>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
+    return pdit::sweep_launch<int32_t, ASYM>(p.maxk, p.wpr, p.tsmem, p.pk, a, p.grid, p.threads, p.smem, st);
+}
+
+int sweep_launch(int dt, bool asym, const Plan &p, const pdit::SweepArgs &a, cudaStream_t st) {
+    return asym ? sweep_launch_t<true>(dt, p, a, st) : sweep_launch_t<false>(dt, p, a, st);
+}
+
+// Scratch-vector length (int32 entries) of a group: swap energies, the row
+// factor of a table update, (general form) its column factor, (concurrent
+// updates) the proposal arrays.
 int sv_len_for(int stride, int cover) { return std::max(stride, cover); }
 
 // Shared-memory slice of one replica group for a given shape: scratch
@@ -112,11 +135,15 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
               bool cupim = false) {
     const int n = h->n;
     const int cover = cover_for(n);
+    const int npad = (n + 3) & ~3;
     p->stride = table_stride(n);
     p->sv_len = sv_len_for(p->stride, cover);
+    p->v2_off = p->sv_len;
+    if (h->asym) p->sv_len += npad;  // column factor of the rank-2 update
     p->cupim_off = p->sv_len;
-    if (cupim) p->sv_len += 3 * ((n + 3) & ~3);  // proposal, energy change, order
-    p->df_bytes = align_up((size_t)2 * n * n * h->dt_bytes, 16);
+    if (cupim) p->sv_len += 3 * npad;  // proposal, energy change, order
+    p->dstride = h->asym ? stage_stride(n, h->dt_bytes) : n;
+    p->df_bytes = align_up((size_t)2 * n * p->dstride * h->dt_bytes, 16);
     const size_t budget = h->smem_optin - reserve;
     const int extra = p->sv_len - sv_len_for(p->stride, cover);
     p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1, extra) <= budget;
@@ -163,7 +190,7 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     p->threads = 32 * wpr * g;
     p->smem = p->df_bytes + (size_t)g * p->group_bytes;
     int bps = 0;
-    int e = sweep_blocks(h->dt_bytes, *p, &bps);
+    int e = sweep_blocks(h->dt_bytes, h->asym != 0, *p, &bps);
     if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
     if (bps < 1) bps = 1;
     if (!p->tsmem) bps = 1;
@@ -204,6 +231,22 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.tables = needs_tables(o, p) ? (int32_t *)take(4 * R * n * (size_t)p.stride) : nullptr;
     w.bytes = off;
     return w;
+}
+
+// The instance and launch-shape fields of a sweep descriptor.
+void fill_shape(pdit::SweepArgs &a, const pdit_qap *h, const Plan &p) {
+    a.D = h->dD;
+    a.F = h->dF;
+    a.n = h->n;
+    a.stride = p.stride;
+    a.dstride = p.dstride;
+    a.zero_diag = h->zero_diag;
+    a.df_bytes = p.df_bytes;
+    a.group_bytes = p.group_bytes;
+    a.sv_len = p.sv_len;
+    a.cupim_off = p.cupim_off;
+    a.v2_off = p.v2_off;
+    a.groups = p.groups;
 }
 
 // ---------------------------------------------------------------------------
@@ -358,11 +401,11 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     if (n < 2 || n > PDIT_N_MAX || !D || !F) return PDIT_EINVAL;
     int64_t maxd = 0, maxf = 0;
     int64_t dlo = D[0], dhi = D[0], flo = F[0], fhi = F[0];
-    bool zd = true;
+    bool zd = true, asym = false;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
             const int32_t d = D[(size_t)i * n + j], f = F[(size_t)i * n + j];
-            if (d != D[(size_t)j * n + i] || f != F[(size_t)j * n + i]) return PDIT_EINVAL;
+            if (d != D[(size_t)j * n + i] || f != F[(size_t)j * n + i]) asym = true;
             dlo = std::min<int64_t>(dlo, d);
             dhi = std::max<int64_t>(dhi, d);
             flo = std::min<int64_t>(flo, f);
@@ -371,13 +414,15 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
             maxf = std::max<int64_t>(maxf, std::llabs((long long)f));
             if (i == j && (d != 0 || f != 0)) zd = false;
         }
-    // |I| <= n maxD maxF, |dE| <= 8 n maxD maxF + 16 maxD maxF, and shifted
-    // energies span twice that: all of it stays inside int32.
+    // |I| <= n maxD maxF (general form: |T| <= 2 n maxD maxF), |dE| <= 8 n
+    // maxD maxF + 16 maxD maxF, and shifted energies span twice that: all of
+    // it stays inside int32.
     if ((int64_t)16 * (n + 2) * maxd * maxf >= ((int64_t)1 << 31)) return PDIT_ERANGE;
     pdit_qap *h = new (std::nothrow) pdit_qap();
     if (!h) return PDIT_ENOMEM;
     h->n = n;
     h->zero_diag = zd ? 1 : 0;
+    h->asym = asym ? 1 : 0;
     h->packed_ok = (dhi - dlo <= 127 && fhi - flo <= 127) ? 1 : 0;
     const int64_t mx = std::max(maxd, maxf);
     h->dt_bytes = mx <= 127 ? 1 : (mx <= 32767 ? 2 : 4);
@@ -502,11 +547,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     }
 
     pdit::SweepArgs a{};
-    a.D = h->dD;
-    a.F = h->dF;
-    a.n = h->n;
-    a.stride = plan.stride;
-    a.zero_diag = h->zero_diag;
+    fill_shape(a, h, plan);
     a.replicas = R;
     a.key0 = (uint32_t)o->seed;
     a.key1 = (uint32_t)(o->seed >> 32);
@@ -524,11 +565,6 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.tables = w.tables;
     a.queue = w.queue;
     a.status = w.status;
-    a.df_bytes = plan.df_bytes;
-    a.group_bytes = plan.group_bytes;
-    a.sv_len = plan.sv_len;
-    a.cupim_off = plan.cupim_off;
-    a.groups = plan.groups;
     a.target = o->target;
     a.reach_ns = (unsigned long long *)o->reach_ns;
     a.reach_sweep = o->reach_sweep;
@@ -551,7 +587,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.dump = (next == se) ? o->tables : nullptr;
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
-            const int e = sweep_launch(h->dt_bytes, plan, a, st);
+            const int e = sweep_launch(h->dt_bytes, h->asym != 0, plan, a, st);
             if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
         }
         if (pt && next < se + 1 && next % o->exchange_period == 0 && next > s) {
@@ -630,24 +666,28 @@ int pdit_beta_max(const pdit_qap *h, double *beta_max) {
     if (!h || !beta_max) return PDIT_EINVAL;
     const int n = h->n;
     const int32_t *D = h->hD.data(), *F = h->hF.data();
-    // Identity permutation: I[m][c] = sum_j D[m][j] F[c][j].
-    std::vector<int64_t> I((size_t)n * n, 0);
+    // Identity permutation: T[m][c] = sum_j D[m][j] F[c][j] + D[j][m] F[j][c]
+    // (the two-term table; 2 I for symmetric D and F).
+    std::vector<int64_t> T((size_t)n * n, 0);
     for (int m = 0; m < n; ++m)
         for (int j = 0; j < n; ++j) {
-            const int64_t d = D[(size_t)m * n + j];
-            if (!d) continue;
-            for (int c = 0; c < n; ++c) I[(size_t)m * n + c] += d * F[(size_t)c * n + j];
+            const int64_t d_out = D[(size_t)m * n + j], d_in = D[(size_t)j * n + m];
+            if (!d_out && !d_in) continue;
+            for (int c = 0; c < n; ++c)
+                T[(size_t)m * n + c] += d_out * F[(size_t)c * n + j] + d_in * F[(size_t)j * n + c];
         }
     double sum = 0.0;
     long long cnt = 0;
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
-            // Eq. 3 with a = i, b = j (identity permutation), symmetric D and F.
-            const int64_t t = I[(size_t)i * n + j] - I[(size_t)i * n + i] + I[(size_t)j * n + i] -
-                              I[(size_t)j * n + j];
-            const int64_t dd = (int64_t)D[(size_t)i * n + i] + D[(size_t)j * n + j] - 2 * (int64_t)D[(size_t)i * n + j];
-            const int64_t ff = (int64_t)F[(size_t)i * n + i] + F[(size_t)j * n + j] - 2 * (int64_t)F[(size_t)i * n + j];
-            const int64_t de = 2 * t + dd * ff;
+            // Eq. 3 with a = i, b = j (identity permutation).
+            const int64_t t = T[(size_t)i * n + j] - T[(size_t)i * n + i] + T[(size_t)j * n + i] -
+                              T[(size_t)j * n + j];
+            const int64_t dd = (int64_t)D[(size_t)i * n + i] + D[(size_t)j * n + j] - D[(size_t)i * n + j] -
+                               D[(size_t)j * n + i];
+            const int64_t ff = (int64_t)F[(size_t)i * n + i] + F[(size_t)j * n + j] - F[(size_t)i * n + j] -
+                               F[(size_t)j * n + i];
+            const int64_t de = t + dd * ff;
             if (de > 0) {
                 sum += (double)de;
                 ++cnt;
@@ -923,7 +963,7 @@ int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas,
     a.df_bytes = plan.df_bytes;
     a.group_bytes = plan.group_bytes;
     a.sv_len = plan.sv_len;
-    const int e = sweep_launch(4, plan, a, st);
+    const int e = sweep_launch(4, false, plan, a, st);
     if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
     finalize_kernel<<<1, 1024, 0, st>>>(replicas, n, w.best_energy, w.best_perm, best_perm, best_cost,
                                         w.status, nullptr);
@@ -950,7 +990,7 @@ struct BatchOut {
 
 struct BatchClass {
     int dt = 1, maxk = 1, wpr = 1, pk = 1;
-    bool tsmem = true;
+    bool tsmem = true, asym = false;
     int threads = 32, grid = 1, nunits = 0;
     size_t smem = 0;
     std::vector<int> items;
@@ -959,21 +999,36 @@ struct BatchClass {
     cudaEvent_t done = nullptr;
 };
 
-int batch_blocks(int dt, const BatchClass &c, int *blocks) {
-    if (dt == 1) return pdit::batch_blocks_per_sm<int8_t>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
-    if (dt == 2) return pdit::batch_blocks_per_sm<int16_t>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
-    return pdit::batch_blocks_per_sm<int32_t>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
+template <bool ASYM>
+int batch_blocks_t(const BatchClass &c, int *blocks) {
+    if (c.dt == 1) return pdit::batch_blocks_per_sm<int8_t, ASYM>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
+    if (c.dt == 2) return pdit::batch_blocks_per_sm<int16_t, ASYM>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
+    return pdit::batch_blocks_per_sm<int32_t, ASYM>(c.maxk, c.wpr, c.tsmem, c.pk, c.threads, c.smem, blocks);
+}
+
+int batch_blocks(const BatchClass &c, int *blocks) {
+    return c.asym ? batch_blocks_t<true>(c, blocks) : batch_blocks_t<false>(c, blocks);
+}
+
+template <bool ASYM>
+int batch_launch_t(const BatchClass &c, const pdit::SweepArgs *descs, int *queue) {
+    if (c.dt == 1)
+        return pdit::batch_launch<int8_t, ASYM>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
+                                                c.grid, c.threads, c.smem, c.stream);
+    if (c.dt == 2)
+        return pdit::batch_launch<int16_t, ASYM>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
+                                                 c.grid, c.threads, c.smem, c.stream);
+    return pdit::batch_launch<int32_t, ASYM>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
+                                             c.grid, c.threads, c.smem, c.stream);
 }
 
 int batch_launch(const BatchClass &c, const pdit::SweepArgs *descs, int *queue) {
-    if (c.dt == 1)
-        return pdit::batch_launch<int8_t>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
-                                          c.grid, c.threads, c.smem, c.stream);
-    if (c.dt == 2)
-        return pdit::batch_launch<int16_t>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
-                                           c.grid, c.threads, c.smem, c.stream);
-    return pdit::batch_launch<int32_t>(c.maxk, c.wpr, c.tsmem, c.pk, descs, c.d_units, c.nunits, queue,
-                                       c.grid, c.threads, c.smem, c.stream);
+    return c.asym ? batch_launch_t<true>(c, descs, queue) : batch_launch_t<false>(c, descs, queue);
+}
+
+// Same compiled kernel shape.
+bool same_class(const BatchClass &x, int dt, bool asym, const Plan &p) {
+    return x.dt == dt && x.asym == asym && x.maxk == p.maxk && x.wpr == p.wpr && x.pk == p.pk && x.tsmem == p.tsmem;
 }
 
 // Per instance: reset its time-to-target outputs and stop flag.
@@ -1127,14 +1182,14 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
     for (int k = 0; k < count; ++k) {
         const Plan &p = plans[k];
         const int dt = items[k].qap->dt_bytes;
+        const bool asym = items[k].qap->asym != 0;
         int found = -1;
-        for (size_t c = 0; c < b->classes.size(); ++c) {
-            const BatchClass &x = b->classes[c];
-            if (x.dt == dt && x.maxk == p.maxk && x.wpr == p.wpr && x.pk == p.pk && x.tsmem == p.tsmem) found = (int)c;
-        }
+        for (size_t c = 0; c < b->classes.size(); ++c)
+            if (same_class(b->classes[c], dt, asym, p)) found = (int)c;
         if (found < 0) {
             BatchClass x;
             x.dt = dt;
+            x.asym = asym;
             x.maxk = p.maxk;
             x.wpr = p.wpr;
             x.pk = p.pk;
@@ -1172,11 +1227,7 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
         const Workspace w = carve(h, &o, p, (char *)b->ws + ws_off[k]);
         pdit::SweepArgs &a = descs[k];
         a = pdit::SweepArgs{};
-        a.D = h->dD;
-        a.F = h->dF;
-        a.n = h->n;
-        a.stride = p.stride;
-        a.zero_diag = h->zero_diag;
+        fill_shape(a, h, p);
         a.replicas = it.replicas;
         a.sweep_begin = 0;
         a.sweep_end = it.sweeps;
@@ -1195,10 +1246,6 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
         a.rung = w.rung;
         a.tables = w.tables;
         a.status = w.status;
-        a.df_bytes = p.df_bytes;
-        a.group_bytes = p.group_bytes;
-        a.sv_len = p.sv_len;
-        a.groups = p.groups;
         a.target = it.target;
         a.reach_ns = (unsigned long long *)it.reach_ns;
         a.reach_sweep = it.reach_sweep;
@@ -1229,7 +1276,7 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
             break;
         }
         int bps = 0;
-        const int qe = batch_blocks(x.dt, x, &bps);
+        const int qe = batch_blocks(x, &bps);
         if (qe != 0) {
             rc = cuda_fail((cudaError_t)qe, "batch occupancy query");
             break;
@@ -1540,11 +1587,7 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
             const Plan &p = r->plan;
             pdit::SweepArgs &a = s->h_descs[k];
             a = pdit::SweepArgs{};
-            a.D = r->qap->dD;
-            a.F = r->qap->dF;
-            a.n = r->n;
-            a.stride = p.stride;
-            a.zero_diag = r->qap->zero_diag;
+            fill_shape(a, r->qap, p);
             a.replicas = r->replicas;
             a.sweep_begin = r->done_sweeps;
             a.sweep_end = std::min(r->sweeps, r->done_sweeps + s->slice);
@@ -1562,20 +1605,16 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
             a.rung = r->w.rung;
             a.tables = r->w.tables;
             a.status = r->w.status;
-            a.df_bytes = p.df_bytes;
-            a.group_bytes = p.group_bytes;
-            a.sv_len = p.sv_len;
-            a.groups = p.groups;
             s->h_outs[k] = BatchOut{r->dperm, r->dcost, r->n, r->replicas, r->w.best_energy, r->w.best_perm};
             const int dt = r->qap->dt_bytes;
+            const bool asym = r->qap->asym != 0;
             int found = -1;
             for (size_t c = 0; c < cls.size(); ++c)
-                if (cls[c].dt == dt && cls[c].maxk == p.maxk && cls[c].wpr == p.wpr && cls[c].pk == p.pk &&
-                    cls[c].tsmem == p.tsmem)
-                    found = (int)c;
+                if (same_class(cls[c], dt, asym, p)) found = (int)c;
             if (found < 0) {
                 BatchClass x;
                 x.dt = dt;
+                x.asym = asym;
                 x.maxk = p.maxk;
                 x.wpr = p.wpr;
                 x.pk = p.pk;
@@ -1611,7 +1650,7 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
             cls[c].stream = s->classes[c].stream;
             cls[c].done = s->classes[c].done;
             int bps = 0;
-            const int qe = batch_blocks(cls[c].dt, cls[c], &bps);
+            const int qe = batch_blocks(cls[c], &bps);
             if (qe != 0) return cuda_fail((cudaError_t)qe, "server occupancy query");
             if (bps < 1 || !cls[c].tsmem) bps = 1;
             cls[c].grid = std::max(1, std::min(cls[c].nunits, s->active[members[c][0]]->qap->num_sms * bps));

@@ -1,4 +1,4 @@
-// Annealed p-dit sweep kernels for the symmetric QAP on sm_103a.
+// Annealed p-dit sweep kernels for the QAP on sm_103a.
 //
 // A replica is owned by a group of G = 32 * WPR threads (WPR warps, 1..8).
 // A CTA stages the instance's D and F once in shared memory (int8/int16/int32,
@@ -20,6 +20,13 @@
 // Sweeps visit locations 0..N-1 in order. Every integer is exact; the only
 // floating point is the weight computation, made of single correctly rounded
 // IEEE operations so the CPU oracle reproduces it bit for bit.
+//
+// General instances (ASYM: D or F not symmetric) keep Eq. 2's two-term table
+// T[m][c] = sum_j D[m][j] F[c][p(j)] + D[j][m] F[p(j)][c] (the negated Eq. 2),
+// take Eq. 3 as printed, and apply each swap as a rank-2 update:
+//   T[m][c] += (D[m][i]-D[m][j*]) (F[c][b]-F[c][a]) + (D[i][m]-D[j*][m]) (F[b][c]-F[a][c]).
+// D and F are then staged with an odd-word row stride so that their columns
+// are read without bank conflicts.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,6 +42,7 @@ struct SweepArgs {
     const int32_t *F;
     int n;
     int stride;     // table row stride S: the smallest 4*odd >= n
+    int dstride;    // row stride (elements) of the staged D and F; n for symmetric instances
     int zero_diag;  // D and F both have zero diagonals
     // run
     int replicas;
@@ -45,6 +53,7 @@ struct SweepArgs {
     int mode;              // 0 anneal (beta[s]), 1 parallel tempering (beta[rung]), 2 fixed (beta[r]),
                            // 3 concurrent updates (beta[s])
     int cupim_off;         // mode 3: offset (int32 entries) of the proposal arrays in the scratch vector
+    int v2_off;            // general form, immediate updates: offset of the second column factor
     const float *beta;
     int fresh;             // start from a Fisher-Yates permutation
     int table_in;          // take the influence table from `tables` instead of rebuilding it
@@ -217,10 +226,11 @@ __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
 // sv = scratch (swap energies in j order, then the rank-1 column factor).
 // Thread t of the group owns candidates t + G k, k < MAXK, and weights
 // t*MAXK .. t*MAXK + MAXK - 1; MAXK is a power of two >= n / G. In table
-// updates lane l of each warp owns rows l + 32 k. PK = pending swaps held
-// before the table is rewritten (1 = immediate rank-1 updates).
+// updates lane l of each warp owns rows l + 32 k. PK = pending rank-1 terms
+// held before the table is rewritten (1 = immediate updates); a swap is one
+// term, or two in the general form (ASYM).
 // ---------------------------------------------------------------------------
-template <typename DT, int MAXK, int WPR, int PK, bool TG = false>
+template <typename DT, int MAXK, int WPR, int PK, bool TG = false, bool ASYM = false>
 __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, int bar,
                                             const DT *sD, const DT *sF, int32_t *T, int32_t *sp,
                                             int32_t *sh, int32_t *sv, uint32_t *upk,
@@ -237,6 +247,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     const int n = a.n;
     const int S = a.stride;
     const int npad = (n + 3) & ~3;
+    const int dn = ASYM ? a.dstride : n;  // row stride of sD, sF
     const uint32_t grep = a.rep_base + (uint32_t)r;
     int32_t *gp = a.perm + (size_t)r * n;
     int32_t *gbp = a.best_perm + (size_t)r * n;
@@ -265,7 +276,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     group_sync<WPR>(bar);
 
     // ---- influence table, Eq. 2 in the one-term form I[m][c] = sum_j D[m][j] F[c][p(j)]
-    // (F symmetric, so row p(j) of F is read contiguously).
+    // (F symmetric, so row p(j) of F is read contiguously); general form:
+    // both terms of Eq. 2, T[m][c] = sum_j D[m][j] F[c][p(j)] + D[j][m] F[p(j)][c].
     if (a.table_in) {
         const int32_t *src = a.tables + (size_t)r * n * S;
         if (src != T) {
@@ -275,12 +287,19 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
         }
     } else {
         for (int m = 0; m < n; ++m) {
-            const DT *Dm = sD + m * n;
+            const DT *Dm = sD + m * dn;
             for (int c0 = 0; c0 < npad; c0 += G) {
                 const int c = c0 + t;
                 int acc = 0;
                 if (c < n) {
-                    for (int j = 0; j < n; ++j) acc += (int)Dm[j] * (int)sF[sp[j] * n + c];
+                    if constexpr (ASYM) {
+                        for (int j = 0; j < n; ++j) {
+                            const int pj = sp[j];
+                            acc += (int)Dm[j] * (int)sF[c * dn + pj] + (int)sD[j * dn + m] * (int)sF[pj * dn + c];
+                        }
+                    } else {
+                        for (int j = 0; j < n; ++j) acc += (int)Dm[j] * (int)sF[sp[j] * n + c];
+                    }
                 }
                 if (c < npad) T[m * S + c] = acc;
             }
@@ -288,7 +307,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     }
     group_sync<WPR>(bar);
 
-    // ---- p-diagonal and energy: E = sum_m I[m][p(m)] (Eq. 1 regrouped)
+    // ---- p-diagonal and energy: E = sum_m I[m][p(m)] (Eq. 1 regrouped);
+    // general form: the sum is 2 E
     long long esum = 0;
     for (int m = t; m < n; m += G) {
         const int h = T[m * S + sp[m]];
@@ -303,6 +323,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
 #pragma unroll
         for (int w = 0; w < WPR; ++w) esum += (long long)gs->wtot[w];
     }
+    if constexpr (ASYM) esum >>= 1;
     long long E, bestE, acc_moves;
     int bsweep;
     bool reached = false;
@@ -331,7 +352,9 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     //   I = T + sum_{q < np} u_q (x) v_q,  u_q[m] = D[i_q][m] - D[j_q][m],
     //   v_q[c] = F[b_q][c] - F[a_q][c]
     // for the np <= 4 accepted swaps (i_q <-> j_q, facilities a_q, b_q) since
-    // the last rewrite of T. upk[m] packs u_0..u_3[m] and vpk[c] packs
+    // the last rewrite of T (general form: two terms per swap, the column
+    // term u[m] = D[m][i_q] - D[m][j_q], v[c] = F[c][b_q] - F[c][a_q] and the
+    // row term above, so T is rewritten every two swaps). upk[m] packs u_0..u_3[m] and vpk[c] packs
     // v_0..v_3[c] as signed bytes (exact: every |u|, |v| <= 127 for the
     // instances this path is chosen for), so one dp4a adds all pending terms
     // of an entry; bytes q >= np are masked off. T is rewritten once per four
@@ -401,25 +424,32 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     // tib, tja: the current I[i][fb], I[js][fa] (thread 0's values are used).
     // Group-uniform; no barrier at the end.
     auto apply_swap = [&](int i, int js, int fa, int fb, int tib, int tja) {
-        const DT *Di = sD + i * n;
-        const DT *Dj = sD + js * n;
-        const DT *Fa = sF + fa * n;
-        const DT *Fb = sF + fb * n;
+        const DT *Di = sD + i * dn;
+        const DT *Dj = sD + js * dn;
+        const DT *Fa = sF + fa * dn;
+        const DT *Fb = sF + fb * dn;
         if constexpr (PK == 1) {
-            // Immediate rank-1 update: lane l of every warp owns rows
-            // l + 32 k; warp w owns column quads w, w + WPR, ...
-            for (int c = t; c < npad; c += G) sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
+            // Immediate rank-1 (general form: rank-2) update: lane l of every
+            // warp owns rows l + 32 k; warp w owns column quads w, w + WPR, ...
+            int32_t *sv2 = sv + a.v2_off;  // column factor of the general form
+            for (int c = t; c < npad; c += G) {
+                sv[c] = c < n ? (int)Fb[c] - (int)Fa[c] : 0;
+                if constexpr (ASYM) sv2[c] = c < n ? (int)sF[c * dn + fb] - (int)sF[c * dn + fa] : 0;
+            }
             if constexpr (TG) {
                 group_sync<WPR>(bar);
-                int4 vq[QL];
+                int4 vq[QL], wq[ASYM ? QL : 1];
 #pragma unroll
                 for (int c2 = 0; c2 < QL; ++c2) {
                     const int cq = lane + 32 * c2;
                     vq[c2] = cq < nq ? reinterpret_cast<const int4 *>(sv)[cq] : make_int4(0, 0, 0, 0);
+                    if constexpr (ASYM)
+                        wq[c2] = cq < nq ? reinterpret_cast<const int4 *>(sv2)[cq] : make_int4(0, 0, 0, 0);
                 }
 #pragma unroll 2
                 for (int m = wg; m < n; m += WPR) {
                     const int um = (int)Di[m] - (int)Dj[m];
+                    const int um2 = ASYM ? (int)sD[m * dn + i] - (int)sD[m * dn + js] : 0;
                     int4 *row = reinterpret_cast<int4 *>(T + m * S);
 #pragma unroll
                     for (int c2 = 0; c2 < QL; ++c2) {
@@ -427,24 +457,30 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         if (cq < nq) {
                             int4 x = row[cq];
                             add_scaled(x, um, vq[c2]);
+                            if constexpr (ASYM) add_scaled(x, um2, wq[ASYM ? c2 : 0]);
                             row[cq] = x;
                         }
                     }
                 }
             } else {
-            int u[ROWS];
+            int u[ROWS], u2[ASYM ? ROWS : 1];
 #pragma unroll
             for (int k = 0; k < ROWS; ++k) {
                 const int m = lane + 32 * k;
                 u[k] = m < n ? (int)Di[m] - (int)Dj[m] : 0;
+                if constexpr (ASYM) u2[k] = m < n ? (int)sD[m * dn + i] - (int)sD[m * dn + js] : 0;
             }
             group_sync<WPR>(bar);
             const int4 *v4 = reinterpret_cast<const int4 *>(sv);
+            const int4 *w4 = reinterpret_cast<const int4 *>(sv2);
             int cq = wg;
             for (; cq + (QB - 1) * WPR < nq; cq += QB * WPR) {
-                int4 vq[QB];
+                int4 vq[QB], wq[ASYM ? QB : 1];
 #pragma unroll
-                for (int b = 0; b < QB; ++b) vq[b] = v4[cq + b * WPR];
+                for (int b = 0; b < QB; ++b) {
+                    vq[b] = v4[cq + b * WPR];
+                    if constexpr (ASYM) wq[b] = w4[cq + b * WPR];
+                }
                 int4 x[ROWS][QB];
 #pragma unroll
                 for (int k = 0; k < ROWS; ++k) {
@@ -461,6 +497,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
 #pragma unroll
                         for (int b = 0; b < QB; ++b) {
                             add_scaled(x[k][b], u[k], vq[b]);
+                            if constexpr (ASYM) add_scaled(x[k][b], u2[ASYM ? k : 0], wq[ASYM ? b : 0]);
                             row[b * WPR] = x[k][b];
                         }
                     }
@@ -468,43 +505,64 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             }
             for (; cq < nq; cq += WPR) {
                 const int4 vq = v4[cq];
+                int4 wq = make_int4(0, 0, 0, 0);
+                if constexpr (ASYM) wq = w4[cq];
 #pragma unroll
                 for (int k = 0; k < ROWS; ++k) {
                     if (lane + 32 * k < n) {
                         int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
                         int4 x = *row;
                         add_scaled(x, u[k], vq);
+                        if constexpr (ASYM) add_scaled(x, u2[ASYM ? k : 0], wq);
                         *row = x;
                     }
                 }
             }
             }
         } else {
-            // Deferred: record u and v of this swap in byte np of upk, vpk.
+            // Deferred: record u and v of this swap in byte np of upk, vpk
+            // (general form: the column term in byte np, the row term in np + 1).
             int8_t *ub = reinterpret_cast<int8_t *>(upk) + np;
             int8_t *vb = reinterpret_cast<int8_t *>(vpk) + np;
             for (int c = t; c < npad; c += G) {
-                ub[4 * c] = (int8_t)(c < n ? (int)Di[c] - (int)Dj[c] : 0);
-                vb[4 * c] = (int8_t)(c < n ? (int)Fb[c] - (int)Fa[c] : 0);
+                if constexpr (ASYM) {
+                    ub[4 * c] = (int8_t)(c < n ? (int)sD[c * dn + i] - (int)sD[c * dn + js] : 0);
+                    vb[4 * c] = (int8_t)(c < n ? (int)sF[c * dn + fb] - (int)sF[c * dn + fa] : 0);
+                    ub[4 * c + 1] = (int8_t)(c < n ? (int)Di[c] - (int)Dj[c] : 0);
+                    vb[4 * c + 1] = (int8_t)(c < n ? (int)Fb[c] - (int)Fa[c] : 0);
+                } else {
+                    ub[4 * c] = (int8_t)(c < n ? (int)Di[c] - (int)Dj[c] : 0);
+                    vb[4 * c] = (int8_t)(c < n ? (int)Fb[c] - (int)Fa[c] : 0);
+                }
             }
         }
         // p-diagonal h[m] = I[m][p(m)] under the new influence and
-        // permutation: h[m] += u_m v[p(m)] where p(m) is unchanged;
-        // the two moved entries from the current I[i][fb], I[js][fa].
-        // Thread 0 writes sp[i], sp[js]; those two are not read here.
+        // permutation: h[m] += u_m v[p(m)] (general form: both terms) where
+        // p(m) is unchanged; the two moved entries from the current I[i][fb],
+        // I[js][fa]. Thread 0 writes sp[i], sp[js]; those two are not read here.
         for (int m = t; m < n; m += G)
             if (m != i && m != js) {
                 const int pm = sp[m];
-                sh[m] += ((int)Di[m] - (int)Dj[m]) * ((int)Fb[pm] - (int)Fa[pm]);
+                int dh = ((int)Di[m] - (int)Dj[m]) * ((int)Fb[pm] - (int)Fa[pm]);
+                if constexpr (ASYM)
+                    dh += ((int)sD[m * dn + i] - (int)sD[m * dn + js]) *
+                          ((int)sF[pm * dn + fb] - (int)sF[pm * dn + fa]);
+                sh[m] += dh;
             }
         if (t == 0) {
             sp[i] = fb;
             sp[js] = fa;
-            sh[i] = tib + ((int)Di[i] - (int)Dj[i]) * ((int)Fb[fb] - (int)Fa[fb]);
-            sh[js] = tja + ((int)Di[js] - (int)Dj[js]) * ((int)Fb[fa] - (int)Fa[fa]);
+            int hi_new = tib + ((int)Di[i] - (int)Dj[i]) * ((int)Fb[fb] - (int)Fa[fb]);
+            int hj_new = tja + ((int)Di[js] - (int)Dj[js]) * ((int)Fb[fa] - (int)Fa[fa]);
+            if constexpr (ASYM) {
+                hi_new += ((int)Di[i] - (int)Di[js]) * ((int)sF[fb * dn + fb] - (int)sF[fb * dn + fa]);
+                hj_new += ((int)Dj[i] - (int)Dj[js]) * ((int)sF[fa * dn + fb] - (int)sF[fa * dn + fa]);
+            }
+            sh[i] = hi_new;
+            sh[js] = hj_new;
         }
         if constexpr (PK > 1) {
-            ++np;
+            np += ASYM ? 2 : 1;
             if (np == PK) {
                 group_sync<WPR>(bar);  // packed factors and thread 0's table reads complete
                 flush();
@@ -544,8 +602,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         (unsigned long long)__shfl_sync(kFull, rw.x, q);
                     const int fa = sp[i];
                     const int hi = sh[i];
-                    const DT *Di = sD + i * n;
-                    const DT *Fa = sF + fa * n;
+                    const DT *Di = sD + i * dn;
+                    const DT *Fa = sF + fa * dn;
                     int ui4 = 0, vfa4 = 0;
                     if constexpr (PK > 1) {
                         ui4 = (int)(upk[i] & pmask);
@@ -567,12 +625,23 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                                 row_ib = __dp4a(ui4, (int)vpk[b], row_ib);
                                 col_ja = __dp4a((int)(upk[j] & pmask), vfa4, col_ja);
                             }
-                            d = 2 * (row_ib - hi + col_ja - sh[j]);
-                            if (zero_diag)
-                                d += 4 * dij * fab;
-                            else
-                                d += ((int)Di[i] + (int)sD[j * n + j] - 2 * dij) *
-                                     ((int)Fa[fa] + (int)sF[b * n + b] - 2 * fab);
+                            if constexpr (ASYM) {
+                                const int dji = sD[j * dn + i];
+                                const int fba = sF[b * dn + fa];
+                                d = row_ib - hi + col_ja - sh[j];
+                                if (zero_diag)
+                                    d += (dij + dji) * (fab + fba);
+                                else
+                                    d += ((int)Di[i] + (int)sD[j * dn + j] - dij - dji) *
+                                         ((int)Fa[fa] + (int)sF[b * dn + b] - fab - fba);
+                            } else {
+                                d = 2 * (row_ib - hi + col_ja - sh[j]);
+                                if (zero_diag)
+                                    d += 4 * dij * fab;
+                                else
+                                    d += ((int)Di[i] + (int)sD[j * n + j] - 2 * dij) *
+                                         ((int)Fa[fa] + (int)sF[b * n + b] - 2 * fab);
+                            }
                             if (j == i) d = 0;
                             lmin = min(lmin, d);
                         }
@@ -664,14 +733,26 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         rowv = __dp4a((int)(upk[i] & m4), (int)vpk[fb], rowv);
                         colv = __dp4a((int)(upk[js] & m4), (int)vpk[fa], colv);
                     }
-                    const int dij = sD[i * n + js];
-                    const int fab = sF[fa * n + fb];
-                    int d = 2 * (rowv - sh[i] + colv - sh[js]);
-                    if (zero_diag)
-                        d += 4 * dij * fab;
-                    else
-                        d += ((int)sD[i * n + i] + (int)sD[js * n + js] - 2 * dij) *
-                             ((int)sF[fa * n + fa] + (int)sF[fb * n + fb] - 2 * fab);
+                    const int dij = sD[i * dn + js];
+                    const int fab = sF[fa * dn + fb];
+                    int d;
+                    if constexpr (ASYM) {
+                        const int dji = sD[js * dn + i];
+                        const int fba = sF[fb * dn + fa];
+                        d = rowv - sh[i] + colv - sh[js];
+                        if (zero_diag)
+                            d += (dij + dji) * (fab + fba);
+                        else
+                            d += ((int)sD[i * dn + i] + (int)sD[js * dn + js] - dij - dji) *
+                                 ((int)sF[fa * dn + fa] + (int)sF[fb * dn + fb] - fab - fba);
+                    } else {
+                        d = 2 * (rowv - sh[i] + colv - sh[js]);
+                        if (zero_diag)
+                            d += 4 * dij * fab;
+                        else
+                            d += ((int)sD[i * n + i] + (int)sD[js * n + js] - 2 * dij) *
+                                 ((int)sF[fa * n + fa] + (int)sF[fb * n + fb] - 2 * fab);
+                    }
                     gs->sel_d = d;
                     gs->aux0 = rowv;
                     gs->aux1 = colv;
@@ -704,8 +785,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     (unsigned long long)__shfl_sync(kFull, rw.x, ii);
                 const int fa = sp[i];
                 const int hi = sh[i];
-                const DT *Di = sD + i * n;
-                const DT *Fa = sF + fa * n;
+                const DT *Di = sD + i * dn;
+                const DT *Fa = sF + fa * dn;
                 // pending factors at this location: packed u_q[i] and v_q[fa]
                 const uint32_t pmask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
                 int ui4 = 0, vfa4 = 0;
@@ -729,12 +810,24 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                             row_ib = __dp4a(ui4, (int)vpk[b], row_ib);
                             col_ja = __dp4a((int)(upk[j] & pmask), vfa4, col_ja);
                         }
-                        int d = 2 * (row_ib - hi + col_ja - sh[j]);
-                        if (zero_diag)
-                            d += 4 * dij * fab;
-                        else
-                            d += ((int)Di[i] + (int)sD[j * n + j] - 2 * dij) *
-                                 ((int)Fa[fa] + (int)sF[b * n + b] - 2 * fab);
+                        int d;
+                        if constexpr (ASYM) {
+                            const int dji = sD[j * dn + i];
+                            const int fba = sF[b * dn + fa];
+                            d = row_ib - hi + col_ja - sh[j];
+                            if (zero_diag)
+                                d += (dij + dji) * (fab + fba);
+                            else
+                                d += ((int)Di[i] + (int)sD[j * dn + j] - dij - dji) *
+                                     ((int)Fa[fa] + (int)sF[b * dn + b] - fab - fba);
+                        } else {
+                            d = 2 * (row_ib - hi + col_ja - sh[j]);
+                            if (zero_diag)
+                                d += 4 * dij * fab;
+                            else
+                                d += ((int)Di[i] + (int)sD[j * n + j] - 2 * dij) *
+                                     ((int)Fa[fa] + (int)sF[b * n + b] - 2 * fab);
+                        }
                         if (j == i) d = 0;
                         sv[j] = d;
                         lmin = min(lmin, d);
@@ -882,20 +975,33 @@ struct SweepBounds {
     static constexpr int threads = sweep_bound(MAXK, WPR);
 };
 
-template <typename DT, int MAXK, int WPR, bool TSMEM, int PK>
+// Stage D and F (global int32, n x n) as DT in shared memory with row stride
+// ds (n, or the odd-word stride of the general form).
+template <typename DT, bool ASYM>
+__device__ __forceinline__ void stage_df(const int32_t *D, const int32_t *F, int n, int ds, DT *sD, DT *sF) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        int o = idx;
+        if constexpr (ASYM) {
+            const int m = idx / n;
+            o = m * ds + (idx - m * n);
+        }
+        sD[o] = static_cast<DT>(D[idx]);
+        sF[o] = static_cast<DT>(F[idx]);
+    }
+}
+
+template <typename DT, int MAXK, int WPR, bool TSMEM, int PK, bool ASYM>
 __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int G = 32 * WPR;
     const int n = a.n;
+    const int ds = ASYM ? a.dstride : n;
     const int grp = threadIdx.x / G;
     const int t = threadIdx.x % G;
     const int bar = 1 + grp;  // named barrier of this group (WPR > 1); 0 is __syncthreads
     DT *sD = reinterpret_cast<DT *>(smem);
-    DT *sF = sD + n * n;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        sD[idx] = static_cast<DT>(a.D[idx]);
-        sF[idx] = static_cast<DT>(a.F[idx]);
-    }
+    DT *sF = sD + n * ds;
+    stage_df<DT, ASYM>(a.D, a.F, n, ds, sD, sF);
     __syncthreads();
     unsigned char *gb = smem + a.df_bytes + (size_t)grp * a.group_bytes;
     const int npad = (n + 3) & ~3;
@@ -913,10 +1019,11 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(
         const int item = gs->item;
         if (item >= a.replicas) break;
         if constexpr (TSMEM) {
-            run_replica<DT, MAXK, WPR, PK, false>(a, item, t, bar, sD, sF, sT, sp, sh, sv, upk, vpk, gs);
+            run_replica<DT, MAXK, WPR, PK, false, ASYM>(a, item, t, bar, sD, sF, sT, sp, sh, sv, upk, vpk, gs);
         } else {
-            run_replica<DT, MAXK, WPR, PK, true>(a, item, t, bar, sD, sF,
-                                                 a.tables + (size_t)item * n * a.stride, sp, sh, sv, upk, vpk, gs);
+            run_replica<DT, MAXK, WPR, PK, true, ASYM>(a, item, t, bar, sD, sF,
+                                                       a.tables + (size_t)item * n * a.stride, sp, sh, sv, upk,
+                                                       vpk, gs);
         }
     }
 }
@@ -931,7 +1038,7 @@ struct BatchUnit {
 // Persistent multi-instance kernel: CTAs take units from `queue`; D and F are
 // restaged when the CTA moves to another instance. Every instance of a launch
 // shares the compiled shape (DT, MAXK, WPR, TSMEM, PK).
-template <typename DT, int MAXK, int WPR, bool TSMEM, int PK>
+template <typename DT, int MAXK, int WPR, bool TSMEM, int PK, bool ASYM>
 __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
     batch_kernel(const SweepArgs *__restrict__ descs, const BatchUnit *__restrict__ units, int nunits,
                  int *queue) {
@@ -955,13 +1062,10 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
             int *dst = reinterpret_cast<int *>(&sa);
             for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
             const int n = descs[bu.inst].n;
+            const int ds = ASYM ? descs[bu.inst].dstride : n;
             const int32_t *D = descs[bu.inst].D, *F = descs[bu.inst].F;
             DT *sD = reinterpret_cast<DT *>(smem);
-            DT *sF = sD + n * n;
-            for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-                sD[idx] = static_cast<DT>(D[idx]);
-                sF[idx] = static_cast<DT>(F[idx]);
-            }
+            stage_df<DT, ASYM>(D, F, n, ds, sD, sD + n * ds);
             cur = bu.inst;
         }
         __syncthreads();
@@ -969,7 +1073,7 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
         const int r = bu.r0 + grp;
         if (grp < sa.groups && r < sa.replicas) {
             const DT *sD = reinterpret_cast<const DT *>(smem);
-            const DT *sF = sD + n * n;
+            const DT *sF = sD + n * (ASYM ? sa.dstride : n);
             unsigned char *gb = smem + sa.df_bytes + (size_t)grp * sa.group_bytes;
             const int npad = (n + 3) & ~3;
             GroupScratch *gs = reinterpret_cast<GroupScratch *>(gb);
@@ -981,22 +1085,23 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
             uint32_t *upk = reinterpret_cast<uint32_t *>(sv + sa.sv_len);
             uint32_t *vpk = upk + npad;
             int32_t *T = TSMEM ? sT : sa.tables + (size_t)r * n * sa.stride;
-            run_replica<DT, MAXK, WPR, PK, !TSMEM>(sa, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
+            run_replica<DT, MAXK, WPR, PK, !TSMEM, ASYM>(sa, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
         }
     }
 }
 
-// Host-side entry points, one per storage type of D and F (defined in
-// pdit_sweep_i8.cu, pdit_sweep_i16.cu, pdit_sweep_i32.cu). Return a
+// Host-side entry points, one per storage type of D and F and form
+// (symmetric / general), defined in pdit_sweep_i8.cu, pdit_sweep_i16.cu,
+// pdit_sweep_i32.cu and their pdit_sweep_gen_*.cu counterparts. Return a
 // cudaError_t value; cudaErrorInvalidValue for a shape with no kernel.
-template <typename DT>
+template <typename DT, bool ASYM>
 int sweep_blocks_per_sm(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, int *blocks);
-template <typename DT>
+template <typename DT, bool ASYM>
 int sweep_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid, int threads,
                  size_t smem, cudaStream_t stream);
-template <typename DT>
+template <typename DT, bool ASYM>
 int batch_blocks_per_sm(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, int *blocks);
-template <typename DT>
+template <typename DT, bool ASYM>
 int batch_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *descs, const BatchUnit *units,
                  int nunits, int *queue, int grid, int threads, size_t smem, cudaStream_t stream);
 
@@ -1011,69 +1116,63 @@ int batch_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *descs, 
     X(1, 4, true, 4) X(8, 1, true, 4) X(4, 2, true, 4) X(2, 4, true, 4) X(1, 8, true, 4)         \
     X(8, 1, false, 4) X(4, 2, false, 4) X(2, 4, false, 4) X(1, 8, false, 4)
 
-#define PDIT_INSTANTIATE_SWEEP(DT, SHAPES)                                                       \
-    template <int MAXK, int WPR, bool TSMEM, int PK>                                             \
-    static int sweep_one(const SweepArgs &a, int grid, int threads, size_t smem,                \
-                         cudaStream_t st, int *blocks, bool query) {                             \
-        auto fn = sweep_kernel<DT, MAXK, WPR, TSMEM, PK>;                                        \
-        if (threads > SweepBounds<MAXK, WPR>::threads) return (int)cudaErrorInvalidValue;        \
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                             (int)smem);                                         \
-        if (e != cudaSuccess) return (int)e;                                                     \
-        if (query) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn,         \
-                                                                              threads, smem);    \
-        fn<<<grid, threads, smem, st>>>(a);                                                      \
-        return (int)cudaGetLastError();                                                          \
-    }                                                                                            \
-    static int sweep_dispatch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a,         \
-                              int grid, int threads, size_t smem, cudaStream_t st, int *blocks,  \
-                              bool query) {                                                      \
-        SHAPES(PDIT_CASE)                                                                        \
-        return (int)cudaErrorInvalidValue;                                                       \
-    }                                                                                            \
-    template <>                                                                                  \
-    int sweep_blocks_per_sm<DT>(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, \
-                                int *blocks) {                                                   \
-        SweepArgs dummy{};                                                                       \
-        return sweep_dispatch(maxk, wpr, tsmem, pk, dummy, 0, threads, smem, nullptr, blocks,    \
-                              true);                                                             \
-    }                                                                                            \
-    template <>                                                                                  \
-    int sweep_launch<DT>(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid,    \
-                         int threads, size_t smem, cudaStream_t st) {                            \
-        return sweep_dispatch(maxk, wpr, tsmem, pk, a, grid, threads, smem, st, nullptr, false); \
-    }                                                                                            \
-    template <int MAXK, int WPR, bool TSMEM, int PK>                                             \
-    static int batch_one(const SweepArgs *d, const BatchUnit *u, int nu, int *q, int grid,       \
-                         int threads, size_t smem, cudaStream_t st, int *blocks, bool query) {   \
-        auto fn = batch_kernel<DT, MAXK, WPR, TSMEM, PK>;                                        \
-        if (threads > SweepBounds<MAXK, WPR>::threads) return (int)cudaErrorInvalidValue;        \
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                             (int)smem);                                         \
-        if (e != cudaSuccess) return (int)e;                                                     \
-        if (query) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn,         \
-                                                                              threads, smem);    \
-        fn<<<grid, threads, smem, st>>>(d, u, nu, q);                                            \
-        return (int)cudaGetLastError();                                                          \
-    }                                                                                            \
-    static int batch_dispatch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *d,         \
-                              const BatchUnit *u, int nu, int *q, int grid, int threads,         \
-                              size_t smem, cudaStream_t st, int *blocks, bool query) {           \
-        SHAPES(PDIT_BATCH_CASE)                                                                  \
-        return (int)cudaErrorInvalidValue;                                                       \
-    }                                                                                            \
-    template <>                                                                                  \
-    int batch_blocks_per_sm<DT>(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem, \
-                                int *blocks) {                                                   \
-        return batch_dispatch(maxk, wpr, tsmem, pk, nullptr, nullptr, 0, nullptr, 0, threads,    \
-                              smem, nullptr, blocks, true);                                      \
-    }                                                                                            \
-    template <>                                                                                  \
-    int batch_launch<DT>(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *d,              \
-                         const BatchUnit *u, int nu, int *q, int grid, int threads, size_t smem, \
-                         cudaStream_t st) {                                                      \
-        return batch_dispatch(maxk, wpr, tsmem, pk, d, u, nu, q, grid, threads, smem, st,        \
-                              nullptr, false);                                                   \
+#define PDIT_INSTANTIATE_SWEEP(DT, ASYM, SHAPES)                                                          \
+    template <int MAXK, int WPR, bool TSMEM, int PK>                                                      \
+    static int sweep_one(const SweepArgs &a, int grid, int threads, size_t smem, cudaStream_t st,         \
+                         int *blocks, bool query) {                                                       \
+        auto fn = sweep_kernel<DT, MAXK, WPR, TSMEM, PK, ASYM>;                                           \
+        if (threads > SweepBounds<MAXK, WPR>::threads) return (int)cudaErrorInvalidValue;                 \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return (int)e;                                                              \
+        if (query) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem);  \
+        fn<<<grid, threads, smem, st>>>(a);                                                               \
+        return (int)cudaGetLastError();                                                                   \
+    }                                                                                                     \
+    static int sweep_dispatch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid,        \
+                              int threads, size_t smem, cudaStream_t st, int *blocks, bool query) {       \
+        SHAPES(PDIT_CASE)                                                                                 \
+        return (int)cudaErrorInvalidValue;                                                                \
+    }                                                                                                     \
+    template <>                                                                                           \
+    int sweep_blocks_per_sm<DT, ASYM>(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem,    \
+                                      int *blocks) {                                                      \
+        SweepArgs dummy{};                                                                                \
+        return sweep_dispatch(maxk, wpr, tsmem, pk, dummy, 0, threads, smem, nullptr, blocks, true);      \
+    }                                                                                                     \
+    template <>                                                                                           \
+    int sweep_launch<DT, ASYM>(int maxk, int wpr, bool tsmem, int pk, const SweepArgs &a, int grid,       \
+                               int threads, size_t smem, cudaStream_t st) {                               \
+        return sweep_dispatch(maxk, wpr, tsmem, pk, a, grid, threads, smem, st, nullptr, false);          \
+    }                                                                                                     \
+    template <int MAXK, int WPR, bool TSMEM, int PK>                                                      \
+    static int batch_one(const SweepArgs *d, const BatchUnit *u, int nu, int *q, int grid, int threads,   \
+                         size_t smem, cudaStream_t st, int *blocks, bool query) {                         \
+        auto fn = batch_kernel<DT, MAXK, WPR, TSMEM, PK, ASYM>;                                           \
+        if (threads > SweepBounds<MAXK, WPR>::threads) return (int)cudaErrorInvalidValue;                 \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return (int)e;                                                              \
+        if (query) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem);  \
+        fn<<<grid, threads, smem, st>>>(d, u, nu, q);                                                     \
+        return (int)cudaGetLastError();                                                                   \
+    }                                                                                                     \
+    static int batch_dispatch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *d,                  \
+                              const BatchUnit *u, int nu, int *q, int grid, int threads, size_t smem,     \
+                              cudaStream_t st, int *blocks, bool query) {                                 \
+        SHAPES(PDIT_BATCH_CASE)                                                                           \
+        return (int)cudaErrorInvalidValue;                                                                \
+    }                                                                                                     \
+    template <>                                                                                           \
+    int batch_blocks_per_sm<DT, ASYM>(int maxk, int wpr, bool tsmem, int pk, int threads, size_t smem,    \
+                                      int *blocks) {                                                      \
+        return batch_dispatch(maxk, wpr, tsmem, pk, nullptr, nullptr, 0, nullptr, 0, threads, smem,       \
+                              nullptr, blocks, true);                                                     \
+    }                                                                                                     \
+    template <>                                                                                           \
+    int batch_launch<DT, ASYM>(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *d,                 \
+                               const BatchUnit *u, int nu, int *q, int grid, int threads, size_t smem,    \
+                               cudaStream_t st) {                                                         \
+        return batch_dispatch(maxk, wpr, tsmem, pk, d, u, nu, q, grid, threads, smem, st, nullptr,        \
+                              false);                                                                     \
     }
 
 #define PDIT_CASE(MK, W, TS, K)                                                                  \

@@ -1,0 +1,7 @@
+// Sweep kernels of the general form (D or F not symmetric) with D and F
+// staged as int32_t (see pdit_sweep.cuh).
+#include "pdit_sweep.cuh"
+
+namespace pdit {
+PDIT_INSTANTIATE_SWEEP(int32_t, true, PDIT_SWEEP_SHAPES_ALL)
+}  // namespace pdit

@@ -2,5 +2,5 @@
 #include "pdit_sweep.cuh"
 
 namespace pdit {
-PDIT_INSTANTIATE_SWEEP(int32_t, PDIT_SWEEP_SHAPES_ALL)
+PDIT_INSTANTIATE_SWEEP(int32_t, false, PDIT_SWEEP_SHAPES_ALL)
 }  // namespace pdit

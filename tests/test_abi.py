@@ -45,14 +45,15 @@ def test_qap_create_rejects_bad_instances_before_touching_the_gpu(L):
     assert h.value is None
     # NULL
     assert L.qap_create(12, None, F32.ctypes.data, ctypes.byref(h)) == P.PDIT_EINVAL
-    # asymmetric
-    Da = D32.copy()
-    Da[0, 1] += 1
-    assert L.qap_create(12, Da.ctypes.data, F32.ctypes.data, ctypes.byref(h)) == P.PDIT_EINVAL
-    # int32 overflow risk: 16 (n+2) maxD maxF >= 2^31
+    # int32 overflow risk: 16 (n+2) maxD maxF >= 2^31, symmetric or not (the
+    # general form's two-term table obeys the same bound)
     big = np.full((12, 12), 4000, np.int32)
     np.fill_diagonal(big, 0)
     assert L.qap_create(12, big.ctypes.data, big.ctypes.data, ctypes.byref(h)) == P.PDIT_ERANGE
+    bigA = big.copy()
+    bigA[0, 1] += 1
+    assert L.qap_create(12, bigA.ctypes.data, big.ctypes.data, ctypes.byref(h)) == P.PDIT_ERANGE
+    assert h.value is None
     L.qap_destroy(None)
 
 
