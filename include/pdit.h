@@ -48,6 +48,7 @@ extern "C" {
 #define PDIT_ECUDA (-4)   /* a CUDA runtime call failed; see pdit_last_error() */
 #define PDIT_EDEVICE (-5) /* a device-side consistency audit failed (see PDIT_STATUS_*) */
 #define PDIT_ENOTSUP (-6) /* a valid request this build cannot run */
+#define PDIT_EIO (-7)     /* a file could not be opened, read or written */
 
 /* Largest instance size. */
 #define PDIT_N_MAX 256
@@ -398,6 +399,42 @@ int pdit_server_result(pdit_server *s, int64_t ticket, int *state, int32_t *best
 
 /* pdit_server_destroy -- free the server and every request. NULL-safe. */
 void pdit_server_destroy(pdit_server *s);
+
+/* ---- QAPLIB text layout ------------------------------------------------- */
+
+/*
+ * pdit_read_qaplib -- read an instance in the QAPLIB text layout: the size n,
+ * then the n x n matrix A, then the n x n matrix B, whitespace-separated
+ * decimal integers (rows may wrap across lines). The objective of such a file
+ * is sum_ij A_ij B_{p(i)p(j)}: Eq. 1 with D = A and F = B, so the result of
+ * an anneal maps an index of A to an index of B.
+ *   path    : file name.
+ *   n       : receives n (2 <= n <= PDIT_N_MAX).
+ *   D, F    : caller buffers of `capacity` int32 each, row-major; both NULL to
+ *             read only n (the whole file is still validated).
+ * Errors: PDIT_EINVAL (NULL path or n, one of D/F NULL, n out of range, a
+ * token that is not a decimal integer, a value outside int32, too few or too
+ * many values), PDIT_ENOMEM (capacity < n*n), PDIT_EIO (cannot open). On
+ * error *n is 0 and D, F may be partly written.
+ */
+int pdit_read_qaplib(const char *path, int *n, int32_t *D, int32_t *F, size_t capacity);
+
+/*
+ * pdit_read_qaplib_solution -- read a solution in the QAPLIB layout: "n cost"
+ * then the n entries of the permutation, 1-based. perm (caller buffer of
+ * `capacity` int32, or NULL) receives it 0-based: perm[i] = the index of B
+ * assigned to index i of A (facility at location i).
+ * Errors: PDIT_EINVAL (malformed, not a permutation), PDIT_ENOMEM (capacity
+ * < n), PDIT_EIO.
+ */
+int pdit_read_qaplib_solution(const char *path, int *n, int64_t *cost, int32_t *perm, int capacity);
+
+/*
+ * pdit_write_qaplib_solution -- write "n cost" and perm (0-based input,
+ * written 1-based) in the QAPLIB layout. Errors: PDIT_EINVAL (perm is not a
+ * permutation of 0..n-1, n out of range, NULL), PDIT_EIO.
+ */
+int pdit_write_qaplib_solution(const char *path, int n, int64_t cost, const int32_t *perm);
 
 /* pdit_strerror -- static text for an error code. */
 const char *pdit_strerror(int code);

@@ -379,6 +379,7 @@ const char *pdit_strerror(int code) {
     case PDIT_ECUDA: return "CUDA runtime error";
     case PDIT_EDEVICE: return "device consistency audit failed";
     case PDIT_ENOTSUP: return "not supported by this build";
+    case PDIT_EIO: return "file could not be opened, read or written";
     default: return "unknown error";
     }
 }

@@ -25,6 +25,7 @@ PDIT_ENOMEM = -3
 PDIT_ECUDA = -4
 PDIT_EDEVICE = -5
 PDIT_ENOTSUP = -6
+PDIT_EIO = -7
 PDIT_N_MAX = 256
 PDIT_MODE_ANNEAL = 0
 PDIT_MODE_PT = 1
@@ -164,6 +165,13 @@ def lib():
     L.pdit_server_result.restype = ctypes.c_int
     L.pdit_server_destroy.argtypes = [vp]
     L.pdit_server_destroy.restype = None
+    L.pdit_read_qaplib.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), vp, vp, ctypes.c_size_t]
+    L.pdit_read_qaplib.restype = ctypes.c_int
+    L.pdit_read_qaplib_solution.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int64), vp, ctypes.c_int]
+    L.pdit_read_qaplib_solution.restype = ctypes.c_int
+    L.pdit_write_qaplib_solution.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_int64, vp]
+    L.pdit_write_qaplib_solution.restype = ctypes.c_int
     L.pdit_strerror.argtypes = [ctypes.c_int]
     L.pdit_strerror.restype = ctypes.c_char_p
     L.pdit_last_error.argtypes = []
@@ -257,6 +265,33 @@ def pdit_anneal_host_ptrs(q: Qap, replicas: int, beta_ptr: int, sweeps: int, see
     return lib().pdit_anneal(q.handle, replicas, ctypes.c_void_p(beta_ptr), sweeps,
                              seed & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(perm_ptr),
                              ctypes.c_void_p(cost_ptr))
+
+
+def read_qaplib(path: str):
+    """(D, F) int32 arrays of an instance in the QAPLIB text layout (A, B)."""
+    n = ctypes.c_int(0)
+    _check(lib().pdit_read_qaplib(os.fsencode(path), ctypes.byref(n), None, None, 0), "pdit_read_qaplib")
+    D = np.zeros((n.value, n.value), np.int32)
+    F = np.zeros_like(D)
+    _check(lib().pdit_read_qaplib(os.fsencode(path), ctypes.byref(n), _ptr(D), _ptr(F), D.size),
+           "pdit_read_qaplib")
+    return D, F
+
+
+def read_qaplib_solution(path: str):
+    """(cost, 0-based permutation) of a solution file in the QAPLIB layout."""
+    n = ctypes.c_int(0)
+    cost = ctypes.c_int64(0)
+    perm = np.zeros(PDIT_N_MAX, np.int32)
+    _check(lib().pdit_read_qaplib_solution(os.fsencode(path), ctypes.byref(n), ctypes.byref(cost), _ptr(perm),
+                                           PDIT_N_MAX), "pdit_read_qaplib_solution")
+    return int(cost.value), perm[:n.value].copy()
+
+
+def write_qaplib_solution(path: str, perm, cost: int):
+    perm = np.ascontiguousarray(perm, np.int32)
+    _check(lib().pdit_write_qaplib_solution(os.fsencode(path), perm.size, int(cost), _ptr(perm)),
+           "pdit_write_qaplib_solution")
 
 
 def pdit_set_warps_per_replica(q: Qap, wpr: int):

@@ -173,3 +173,22 @@ def test_batch_mixing_symmetric_and_general_instances():
     b.close()
     for q in qs:
         q.close()
+
+
+def test_qaplib_file_end_to_end(tmp_path):
+    """Read an instance file, anneal it, write and re-read the solution."""
+    p = P()
+    A, B = G.asymmetric_instance(27, seed=11, diag=True)
+    f = tmp_path / "a27.dat"
+    f.write_text("27\n\n" + "\n".join(" ".join(map(str, r)) for r in A) + "\n\n" +
+                 "\n".join(" ".join(map(str, r)) for r in B) + "\n")
+    D, F = p.read_qaplib(str(f))
+    beta = schedule(D, F, 60)
+    with p.Qap(D, F) as q:
+        perm, cost = p.pdit_anneal(q, 16, beta, 60, 2)
+    r = O.anneal(A, B, beta, 60, 2, 0, 16, threads=8)
+    assert cost == r["cost"] and np.array_equal(perm, r["perm"])
+    sln = tmp_path / "a27.sln"
+    p.write_qaplib_solution(str(sln), perm, cost)
+    c2, p2 = p.read_qaplib_solution(str(sln))
+    assert c2 == cost and np.array_equal(p2, perm) and O.cost(A, B, p2) == cost
