@@ -41,6 +41,14 @@ WORKLOADS = {
     "n100": ("n100", 4096, 10000, "linear"),
     "n30": ("n30", 1024, 5000, "geometric"),
     "n12": ("n12", 64, 1000, "linear"),
+    "n100a": ("n100a", 4096, 10000, "linear"),
+    "c256": ("c256", 4096, 2000, "linear"),
+}
+WORKLOAD_TEXT = {
+    "n100": "dense symmetric QAP N=100 (D, F uniform 0..99)",
+    "n100a": "dense asymmetric QAP N=100 (every entry of D and F independent uniform 0..99, zero diagonals)",
+    "c256": "two-level flow N=256 (flow 1 between every pair of a 92-facility subset, 0 elsewhere; "
+            "D dense symmetric uniform 1..99): the structure of the paper's tai256c, synthetic values",
 }
 METRIC = "p-dit updates/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -65,15 +73,17 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def survey_bytes_per_update(n: int, accept_frac: float) -> float:
+def survey_bytes_per_update(n: int, accept_frac: float, general: bool = False) -> float:
     """Algorithmic shared-memory bytes per p-dit update of the method as
     written (every accepted swap rewrites the table): 4 (4N) for the gathers
     (row, column, p-diagonal, permutation, int32) plus, per accepted swap,
-    8 N^2 (table read and write) + 8 N (the two factor vectors)."""
-    return 4 * (4 * n) + accept_frac * (8 * n * n + 8 * n)
+    8 N^2 (table read and write) + 8 N (the two factor vectors; four for the
+    rank-2 update of the general form)."""
+    return 4 * (4 * n) + accept_frac * (8 * n * n + (16 if general else 8) * n)
 
 
-def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pending: int = 1) -> float:
+def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pending: int = 1,
+                                 general: bool = False) -> float:
     """Shared-memory bytes one update must move in this design.
     Immediate table updates (pending = 1):
       gather, every update: p[j], I[i][p(j)], I[j][p(i)], h[j] as int32, plus
@@ -85,14 +95,33 @@ def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pend
     u[j], v[p(j)] (+8 N); an accepted swap writes one byte of each packed
     factor per entry (2 N), reads two D rows and two F rows (4 N dt) and p,
     h (12 N), and a quarter of a table rewrite with its packed factors
-    (2 N^2 + 2 N)."""
+    (2 N^2 + 2 N).
+    General form: the gather also reads D[j][i] and F[p(j)][p(i)] (+2 N dt);
+    a swap reads D and F columns as well (+4 N dt) and carries two rank-1
+    terms (two factor vectors; two of the four pending slots, so half a table
+    rewrite per swap when deferred)."""
     if pending <= 1:
         gather = 16 * n + 2 * n * dt_bytes
         swap = 8 * n * n + 4 * n * dt_bytes + 12 * n
+        if general:
+            gather += 2 * n * dt_bytes
+            swap += 4 * n * dt_bytes + 4 * n
     else:
         gather = 24 * n + 2 * n * dt_bytes
         swap = 2 * n * n + 4 * n * dt_bytes + 16 * n
+        if general:
+            gather += 2 * n * dt_bytes
+            swap += 2 * n * n + 4 * n * dt_bytes + 4 * n
     return gather + accept_frac * swap
+
+
+def class_bytes_per_update(n: int, dt_bytes: int, accept_frac: float) -> float:
+    """Shared-memory bytes per update of the flow-class kernel: per candidate
+    p[j], G[j] and the swap energy written then read back (int32), x[p(j)]
+    (1 byte) and D[i][j] (dt): (17 + dt) N; per accepted swap at most (only
+    swaps across the classes move G) two D rows and G read and written:
+    2 N dt + 8 N."""
+    return (17 + dt_bytes) * n + accept_frac * (2 * n * dt_bytes + 8 * n)
 
 
 class Clocks:
@@ -427,6 +456,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--wpr", type=int, default=0,
                     help="warps per replica (0: the library's choice)")
+    ap.add_argument("--no-class-update", action="store_true",
+                    help="run two-level-flow instances with the table kernels")
     ap.add_argument("--mode", default="anneal", choices=["anneal", "cupim"],
                     help="sequential p-dit sweeps (the paper's PIM) or concurrent updates (its CUPIM)")
     ap.add_argument("--pk", type=int, default=0,
@@ -468,6 +499,10 @@ def main():
     D, F = G.named(inst)
     n = D.shape[0]
     q = P.Qap(D, F)
+    if args.no_class_update:
+        P.pdit_set_class_update(q, False)
+    class_path = (P.pdit_instance_form(q) == P.PDIT_FORM_FLOW_CLASSES and not args.no_class_update
+                  and args.mode != "cupim")
     if args.wpr:
         P.pdit_set_warps_per_replica(q, args.wpr)
     if args.pk:
@@ -559,18 +594,33 @@ def main():
     # roofline of the sweep kernel: shared-memory bound
     props = torch.cuda.get_device_properties(dev)
     dt_bytes = 1 if max(abs(int(D.max())), abs(int(F.max()))) <= 127 else 2
-    bpu = survey_bytes_per_update(n, accept_frac)
-    bpu_design = algorithmic_bytes_per_update(n, dt_bytes, accept_frac, shape["pending_swaps"])
+    general = not (np.array_equal(D, D.T) and np.array_equal(F, F.T))
+    bpu = survey_bytes_per_update(n, accept_frac, general)
+    bpu_design = algorithmic_bytes_per_update(n, dt_bytes, accept_frac, shape["pending_swaps"], general)
+    basis = (("16 N + A (8 N^2 + 16 N): the method's traffic with a rank-2 table rewrite per accepted swap "
+              "(general form)") if general else
+             "16 N + A (8 N^2 + 8 N): the method's traffic with a table rewrite per accepted swap")
+    kname = "sweep_kernel<int8,%d,%d,%s,%d>" % (shape["candidates_per_thread"], shape["warps_per_replica"],
+                                                "smem" if shape["tables_in_smem"] else "global",
+                                                shape["pending_swaps"])
+    if class_path:
+        # the flow-class kernel keeps no table: its own traffic is the figure
+        bpu = bpu_design = class_bytes_per_update(n, dt_bytes, accept_frac)
+        basis = ("(17 + dt) N + A (2 N dt + 8 N): the flow-class kernel's gathers plus, per accepted "
+                 "swap, at most two D rows and the G vector (A counts swaps within a class too)")
+        kname = "class_kernel<int8,%d,%d>" % (shape["candidates_per_thread"], shape["warps_per_replica"])
     kernel_s = tot_ms / 1000.0 / args.steps
     achieved = bpu * upd_rank / kernel_s / 1e9
     sm_mhz = clk.get("sm_mhz") or 0.0
     peak = props.multi_processor_count * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9 if sm_mhz else None
     traffic = None
     try:
-        with open(TRAFFIC_FILE) as fh:
-            tr = json.load(fh)
-        if tr.get("source_sha") == kernel_source_sha():
-            traffic = tr.get("dram_bytes_per_launch")
+        # the stored DRAM counters describe the default workload's kernel only
+        if args.workload == "n100" and args.mode == "anneal" and not args.wpr and not args.pk:
+            with open(TRAFFIC_FILE) as fh:
+                tr = json.load(fh)
+            if tr.get("source_sha") == kernel_source_sha():
+                traffic = tr.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
 
@@ -578,9 +628,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "%s: dense symmetric QAP N=%d (D, F uniform 0..99)" % (args.workload, n)
-                   if args.workload == "n100" else args.workload,
+        "config": {"workload": "%s: %s" % (args.workload, WORKLOAD_TEXT[args.workload])
+                   if args.workload in WORKLOAD_TEXT else args.workload,
                    "mode": args.mode,
+                   "update": "flow classes" if class_path else "table",
                    "replicas_per_gpu": replicas, "sweeps": sweeps, "schedule": kind, "seed": 0,
                    "global_batch": replicas * world, "seq_len": n,
                    "parallelism": "replicas sharded over %d GPU(s)" % world,
@@ -593,13 +644,9 @@ def main():
                    "reasons": clk.get("reasons"), "samples": clk.get("samples")},
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if peak else None, "traffic": traffic,
-                     "kernel": "sweep_kernel<int8,%d,%d,%s,%d>" % (shape["candidates_per_thread"],
-                                                                   shape["warps_per_replica"],
-                                                                   "smem" if shape["tables_in_smem"] else "global",
-                                                                   shape["pending_swaps"]),
+                     "kernel": kname,
                      "bytes_per_update": bpu,
-                     "bytes_per_update_basis": "16 N + A (8 N^2 + 8 N): the method's traffic with a table "
-                                               "rewrite per accepted swap",
+                     "bytes_per_update_basis": basis,
                      "design_bytes_per_update": bpu_design,
                      "design_frac": (bpu_design * upd_rank / kernel_s / 1e9 / peak) if peak else None,
                      "peak_source": "derived: %d SMs x %d B/clk x median SM clock under load (%s MHz)"

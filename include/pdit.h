@@ -120,6 +120,34 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
  */
 int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape);
 
+/* Instance forms (pdit_instance_form). */
+#define PDIT_FORM_SYMMETRIC 0     /* D, F symmetric: one-term table I (Eq. 2 = -2 I) */
+#define PDIT_FORM_GENERAL 1       /* D or F not symmetric: Eq. 2's two-term table, Eq. 3 as printed */
+#define PDIT_FORM_FLOW_CLASSES 2  /* two-level flow (Methods, tai256c): an N-vector instead of the table */
+
+/*
+ * pdit_instance_form -- how the kernels treat this instance, decided at
+ * qap_create: PDIT_FORM_FLOW_CLASSES when D is symmetric with a zero diagonal
+ * and every off-diagonal flow is F[c][d] = f0 + f x_c x_d for some x in
+ * {0,1}^n (the structure the Methods section exploits for tai256c: a swap
+ * within a class leaves the energy unchanged, and every swap across the
+ * classes has an energy change that depends only on the two locations); then
+ * the influence table collapses to G[m] = sum over locations j holding a
+ * class-1 facility of D[m][j], and an accepted swap costs O(n) instead of
+ * O(n^2). Results are identical to the table path's (the swap energies are
+ * the same exact integers). Concurrent-update mode and calls that request the
+ * table dump run the table kernels. Returns the form or PDIT_EINVAL.
+ */
+int pdit_instance_form(const pdit_qap *h);
+
+/*
+ * pdit_set_class_update -- enable (1, the default) or disable (0) the
+ * flow-class kernel for later calls on this handle; disabled, a
+ * PDIT_FORM_FLOW_CLASSES instance runs the table kernels. Results do not
+ * depend on it. Errors: PDIT_EINVAL.
+ */
+int pdit_set_class_update(pdit_qap *h, int enable);
+
 /*
  * pdit_set_pending_swaps -- table-update batching of later calls on this
  * handle: k = 1 rewrites the influence table after every accepted swap

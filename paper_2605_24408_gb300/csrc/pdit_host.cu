@@ -23,6 +23,11 @@ struct pdit_qap {
     int dt_bytes = 4;       // storage of D and F in shared memory: 1, 2 or 4 bytes
     int zero_diag = 0;
     int asym = 0;           // D or F not symmetric: the general form (two-term table)
+    int cls = 0;            // two-level flow (pdit_class.cu): F = f0 + f x_c x_d off the diagonal
+    int use_cls = 1;        // run such instances with the flow-class kernel
+    int cls_f = 0;
+    long long cls_e0 = 0;
+    uint8_t *dx = nullptr;  // x_c on the device
     int packed_ok = 0;      // max-min of D and of F <= 127: swap factors fit int8
     std::vector<int32_t> hD, hF;
     int32_t *dD = nullptr, *dF = nullptr;
@@ -84,8 +89,9 @@ int stage_stride(int n, int dt) {
 
 struct Plan {
     int maxk = 1, wpr = 1, pk = 1;
-    bool tsmem = true;
+    bool tsmem = true, cls = false;
     int stride = 0, sv_len = 0, cupim_off = 0, v2_off = 0, dstride = 0;
+    size_t table_elems = 0;  // int32 entries of one replica's saved table (workspace)
     size_t df_bytes = 0, group_bytes = 0, smem = 0;
     int groups = 1, threads = 32, grid = 1;
 };
@@ -137,16 +143,15 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     const int cover = cover_for(n);
     const int npad = (n + 3) & ~3;
     p->stride = table_stride(n);
-    p->sv_len = sv_len_for(p->stride, cover);
-    p->v2_off = p->sv_len;
-    if (h->asym) p->sv_len += npad;  // column factor of the rank-2 update
-    p->cupim_off = p->sv_len;
-    if (cupim) p->sv_len += 3 * npad;  // proposal, energy change, order
+    const int base = sv_len_for(p->stride, cover);
+    // Extra scratch-vector entries for `k` pending terms: the column factor
+    // of the general form's immediate rank-2 update, and the proposal,
+    // energy-change and order arrays of concurrent updates.
+    auto extra_for = [&](int k) { return (h->asym && k == 1 ? npad : 0) + (cupim ? 3 * npad : 0); };
     p->dstride = h->asym ? stage_stride(n, h->dt_bytes) : n;
     p->df_bytes = align_up((size_t)2 * n * p->dstride * h->dt_bytes, 16);
     const size_t budget = h->smem_optin - reserve;
-    const int extra = p->sv_len - sv_len_for(p->stride, cover);
-    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1, extra) <= budget;
+    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1, extra_for(1)) <= budget;
     if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;
     const bool defer_ok = h->packed_ok != 0;
     if (pk != 0 && pk != 1 && pk != 4) return PDIT_EINVAL;
@@ -156,13 +161,17 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
         // (tables in shared memory), and always for tables in global memory.
         pk = 1;
         if (defer_ok) {
-            const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1, extra);
-            const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4, extra);
-            if (!p->tsmem || (budget - p->df_bytes) / g4 == (budget - p->df_bytes) / g1) pk = 4;
+            const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1, extra_for(1));
+            const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4, extra_for(4));
+            if (!p->tsmem || (budget - p->df_bytes) / g4 >= (budget - p->df_bytes) / g1) pk = 4;
         }
     }
     p->pk = pk;
-    p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk, extra);
+    p->table_elems = (size_t)n * p->stride;
+    p->v2_off = base;
+    p->cupim_off = base + (h->asym && pk == 1 ? npad : 0);
+    p->sv_len = base + extra_for(pk);
+    p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk, extra_for(pk));
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
     int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
     if (!p->tsmem && h->l2_bytes > 0 && h->num_sms > 0) {
@@ -199,6 +208,66 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     return PDIT_OK;
 }
 
+// Launch shape of the flow-class kernel: D as DT and x in shared memory once
+// per CTA, then per replica group: scratch, p, G and the swap energies.
+int make_class_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
+    const int n = h->n;
+    const int cover = cover_for(n);
+    const int npad = (n + 3) & ~3;
+    p->cls = true;
+    p->tsmem = true;
+    p->pk = 1;
+    p->stride = npad;
+    p->table_elems = (size_t)npad;  // G
+    p->sv_len = cover;
+    p->dstride = n;
+    p->df_bytes = align_up((size_t)n * n * h->dt_bytes, 16) + align_up((size_t)npad, 16);
+    p->group_bytes = align_up(pdit::kScratchBytes + (size_t)4 * (2 * npad + cover), 16);
+    const size_t budget = h->smem_optin;
+    if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
+    const int fit = (int)((budget - p->df_bytes) / p->group_bytes);
+    if (wpr <= 0) wpr = 1;  // one warp per replica: many independent replicas per SM
+    if (wpr < 1 || wpr > cover / 32 || (wpr & (wpr - 1))) return PDIT_EINVAL;
+    p->wpr = wpr;
+    p->maxk = cover / (32 * wpr);
+    int g = std::min(fit, pdit::class_bound(p->maxk, wpr) / (32 * wpr));
+    if (wpr > 1) g = std::min(g, 15);  // named barriers 1..15
+    const int per_sm = (replicas + h->num_sms - 1) / h->num_sms;
+    g = std::max(1, std::min(g, per_sm));
+    p->groups = g;
+    p->threads = 32 * wpr * g;
+    p->smem = p->df_bytes + (size_t)g * p->group_bytes;
+    int bps = 0;
+    int e = 0;
+    if (h->dt_bytes == 1) e = pdit::class_blocks_per_sm<int8_t>(p->maxk, wpr, p->threads, p->smem, &bps);
+    else if (h->dt_bytes == 2) e = pdit::class_blocks_per_sm<int16_t>(p->maxk, wpr, p->threads, p->smem, &bps);
+    else e = pdit::class_blocks_per_sm<int32_t>(p->maxk, wpr, p->threads, p->smem, &bps);
+    if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
+    if (bps < 1) bps = 1;
+    const int need = (replicas + g - 1) / g;
+    p->grid = std::max(1, std::min(need, h->num_sms * bps));
+    return PDIT_OK;
+}
+
+int class_launch(int dt, const Plan &p, const pdit::SweepArgs &a, cudaStream_t st) {
+    if (dt == 1) return pdit::class_launch<int8_t>(p.maxk, p.wpr, a, p.grid, p.threads, p.smem, st);
+    if (dt == 2) return pdit::class_launch<int16_t>(p.maxk, p.wpr, a, p.grid, p.threads, p.smem, st);
+    return pdit::class_launch<int32_t>(p.maxk, p.wpr, a, p.grid, p.threads, p.smem, st);
+}
+
+// Whether a call runs the flow-class kernel: a two-level-flow instance with
+// the path enabled, in a sequential mode, without a request for the N x N
+// table dump (which only the table kernels keep).
+bool use_class_path(const pdit_qap *h, const pdit_opts *o) {
+    return h->cls && h->use_cls && o->mode != PDIT_MODE_CUPIM && !o->tables;
+}
+
+// Launch plan of a call: the flow-class kernel or the table kernels.
+int plan_for(const pdit_qap *h, const pdit_opts *o, Plan *p) {
+    if (use_class_path(h, o)) return make_class_plan(h, o->replicas, h->force_wpr, p);
+    return make_plan(h, o->replicas, h->force_wpr, h->force_pk, p, 0, o->mode == PDIT_MODE_CUPIM);
+}
+
 struct Workspace {
     int32_t *perm, *best_perm, *best_sweep, *rung, *since_top, *queue, *status, *tables, *done;
     int64_t *energy, *best_energy, *accepted;
@@ -228,7 +297,7 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.queue = (int32_t *)take(4 * 64);
     w.status = (int32_t *)take(4);
     w.done = (int32_t *)take(4);
-    w.tables = needs_tables(o, p) ? (int32_t *)take(4 * R * n * (size_t)p.stride) : nullptr;
+    w.tables = needs_tables(o, p) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
     w.bytes = off;
     return w;
 }
@@ -247,6 +316,9 @@ void fill_shape(pdit::SweepArgs &a, const pdit_qap *h, const Plan &p) {
     a.cupim_off = p.cupim_off;
     a.v2_off = p.v2_off;
     a.groups = p.groups;
+    a.cls_x = h->dx;
+    a.cls_f = h->cls_f;
+    a.cls_e0 = h->cls_e0;
 }
 
 // ---------------------------------------------------------------------------
@@ -347,6 +419,56 @@ __global__ void finalize_kernel(int replicas, int n, const int64_t *best_energy,
     for (int m = threadIdx.x; m < n; m += blockDim.x) out_perm[m] = best_perm[(size_t)winner * n + m];
 }
 
+// Two-level flow (the Methods section's tai256c structure): D symmetric with a
+// zero diagonal and F[c][d] = f0 + f x_c x_d for every c != d with x_c in
+// {0, 1}. Fills x, f0, f and returns true when (D, F) has this form.
+bool detect_flow_classes(int n, const int32_t *D, const int32_t *F, std::vector<uint8_t> &x, int64_t &f0,
+                         int64_t &f) {
+    for (int i = 0; i < n; ++i) {
+        if (D[(size_t)i * n + i] != 0) return false;
+        for (int j = i + 1; j < n; ++j)
+            if (D[(size_t)i * n + j] != D[(size_t)j * n + i]) return false;
+    }
+    int64_t v[2] = {0, 0};
+    int nv = 0;
+    for (int c = 0; c < n; ++c)
+        for (int d = 0; d < n; ++d) {
+            if (c == d) continue;
+            const int64_t val = F[(size_t)c * n + d];
+            if (nv > 0 && val == v[0]) continue;
+            if (nv > 1 && val == v[1]) continue;
+            if (nv == 2) return false;
+            v[nv++] = val;
+        }
+    x.assign((size_t)n, 0);
+    if (nv == 1) {
+        f0 = v[0];
+        f = 0;
+        return true;
+    }
+    for (int pick = 0; pick < 2; ++pick) {
+        const int64_t in = v[pick], out = v[1 - pick];
+        for (int c = 0; c < n; ++c) {
+            x[c] = 0;
+            for (int d = 0; d < n; ++d)
+                if (d != c && F[(size_t)c * n + d] == in) x[c] = 1;
+        }
+        bool ok = true;
+        for (int c = 0; c < n && ok; ++c)
+            for (int d = 0; d < n; ++d)
+                if (d != c && F[(size_t)c * n + d] != ((x[c] && x[d]) ? in : out)) {
+                    ok = false;
+                    break;
+                }
+        if (ok) {
+            f0 = out;
+            f = in - out;
+            return true;
+        }
+    }
+    return false;
+}
+
 int validate_opts(const pdit_qap *h, const pdit_opts *o) {
     if (!h || !o) return PDIT_EINVAL;
     if (o->struct_size != sizeof(pdit_opts)) return PDIT_EINVAL;
@@ -424,6 +546,15 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     h->n = n;
     h->zero_diag = zd ? 1 : 0;
     h->asym = asym ? 1 : 0;
+    std::vector<uint8_t> cx;
+    int64_t f0 = 0, fcls = 0;
+    if (!asym && detect_flow_classes(n, D, F, cx, f0, fcls)) {
+        int64_t dsum = 0;
+        for (size_t k = 0; k < (size_t)n * n; ++k) dsum += D[k];
+        h->cls = 1;
+        h->cls_f = (int)fcls;
+        h->cls_e0 = f0 * dsum;  // D's diagonal is zero
+    }
     h->packed_ok = (dhi - dlo <= 127 && fhi - flo <= 127) ? 1 : 0;
     const int64_t mx = std::max(maxd, maxf);
     h->dt_bytes = mx <= 127 ? 1 : (mx <= 32767 ? 2 : 4);
@@ -441,6 +572,10 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dF, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(h->dD, D, bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->dF, F, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && h->cls) {
+        e = cudaMalloc((void **)&h->dx, (size_t)n);
+        if (e == cudaSuccess) e = cudaMemcpy(h->dx, cx.data(), (size_t)n, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         const int rc = (e == cudaErrorMemoryAllocation) ? PDIT_ENOMEM : cuda_fail(e, "qap_create");
         qap_destroy(h);
@@ -458,6 +593,7 @@ void qap_destroy(pdit_qap *h) {
     if (h->stream) cudaStreamDestroy(h->stream);
     cudaFree(h->dD);
     cudaFree(h->dF);
+    cudaFree(h->dx);
     cudaFree(h->ws);
     cudaFree(h->dbeta);
     cudaFree(h->dperm);
@@ -479,7 +615,8 @@ int pdit_set_warps_per_replica(pdit_qap *h, int wpr) {
 int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape) {
     if (!h || replicas < 1 || !shape) return PDIT_EINVAL;
     Plan p;
-    const int rc = make_plan(h, replicas, h->force_wpr, h->force_pk, &p);
+    const int rc = (h->cls && h->use_cls) ? make_class_plan(h, replicas, h->force_wpr, &p)
+                                          : make_plan(h, replicas, h->force_wpr, h->force_pk, &p);
     if (rc) return rc;
     shape[0] = p.wpr;
     shape[1] = p.maxk;
@@ -488,6 +625,18 @@ int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape) {
     shape[4] = p.tsmem ? 1 : 0;
     shape[5] = (int)p.smem;
     shape[6] = p.pk;
+    return PDIT_OK;
+}
+
+int pdit_instance_form(const pdit_qap *h) {
+    if (!h) return PDIT_EINVAL;
+    if (h->cls) return PDIT_FORM_FLOW_CLASSES;
+    return h->asym ? PDIT_FORM_GENERAL : PDIT_FORM_SYMMETRIC;
+}
+
+int pdit_set_class_update(pdit_qap *h, int enable) {
+    if (!h || (enable != 0 && enable != 1)) return PDIT_EINVAL;
+    h->use_cls = enable;
     return PDIT_OK;
 }
 
@@ -500,7 +649,7 @@ int pdit_set_pending_swaps(pdit_qap *h, int k) {
 size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o) {
     if (!h || !o || o->replicas < 1) return 0;
     Plan p;
-    if (make_plan(h, o->replicas, h->force_wpr, h->force_pk, &p, 0, o->mode == PDIT_MODE_CUPIM) != PDIT_OK) return 0;
+    if (plan_for(h, o, &p) != PDIT_OK) return 0;
     return carve(h, o, p, nullptr).bytes;
 }
 
@@ -508,7 +657,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     int rc = validate_opts(h, o);
     if (rc) return rc;
     Plan plan;
-    rc = make_plan(h, o->replicas, h->force_wpr, h->force_pk, &plan, 0, o->mode == PDIT_MODE_CUPIM);
+    rc = plan_for(h, o, &plan);
     if (rc) return rc;
     const size_t need = carve(h, o, plan, nullptr).bytes;
     char *base = (char *)o->workspace;
@@ -588,7 +737,8 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.dump = (next == se) ? o->tables : nullptr;
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
-            const int e = sweep_launch(h->dt_bytes, h->asym != 0, plan, a, st);
+            const int e = plan.cls ? class_launch(h->dt_bytes, plan, a, st)
+                                   : sweep_launch(h->dt_bytes, h->asym != 0, plan, a, st);
             if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
         }
         if (pt && next < se + 1 && next % o->exchange_period == 0 && next > s) {
@@ -714,10 +864,13 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     float best_ms = 0.0f;
     for (int wpr = 1; wpr <= cover / 32 && wpr <= 8 && e == cudaSuccess && rc == PDIT_OK; wpr <<= 1)
         for (int pk = 1; pk <= 4 && e == cudaSuccess && rc == PDIT_OK; pk += 3) {
+            const bool cls = h->cls && h->use_cls;
+            if (cls && pk != 1) continue;  // the flow-class kernel keeps no table
             h->force_wpr = wpr;
             h->force_pk = pk;
             Plan p;
-            if (make_plan(h, replicas, wpr, pk, &p) != PDIT_OK) continue;
+            if ((cls ? make_class_plan(h, replicas, wpr, &p) : make_plan(h, replicas, wpr, pk, &p)) != PDIT_OK)
+                continue;
             pdit_opts o;
             pdit_opts_init(&o);
             o.replicas = replicas;

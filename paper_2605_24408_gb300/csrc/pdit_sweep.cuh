@@ -54,6 +54,10 @@ struct SweepArgs {
                            // 3 concurrent updates (beta[s])
     int cupim_off;         // mode 3: offset (int32 entries) of the proposal arrays in the scratch vector
     int v2_off;            // general form, immediate updates: offset of the second column factor
+    // flow classes (pdit_class.cu): F[c][d] = f0 + f x_c x_d off the diagonal
+    const uint8_t *cls_x;  // x_c of every facility
+    int cls_f;             // f
+    long long cls_e0;      // f0 * sum over i != j of D[i][j]
     const float *beta;
     int fresh;             // start from a Fisher-Yates permutation
     int table_in;          // take the influence table from `tables` instead of rebuilding it
@@ -87,10 +91,10 @@ struct SweepArgs {
 struct GroupScratch {
     unsigned long long wtot[8];
     int wmin[8];
-    int sel_j, sel_d;
+    int sel_j, sel_d, sel_f;  // the drawn outcome: location, energy change, its facility
     int item;
     int stop;
-    int cnt, aux0, aux1, aux2;
+    int cnt, aux0, aux1;
 };
 constexpr size_t kScratchBytes = sizeof(GroupScratch);  // 128
 
@@ -212,6 +216,126 @@ __device__ __forceinline__ void note_target(const SweepArgs &a, long long bestE,
     if (a.done) atomicExch(a.done, 1);
 }
 
+// Initial permutation of global replica `grep` into sp (reading R5):
+// Fisher-Yates from the last position down; step k uses word k%4 of
+// Philox(inst, replica, 0xFFFFFFFF, k/4) and index floor(u (k+1) / 2^32).
+// sv receives the random words. No barrier at the end.
+template <int WPR>
+__device__ __forceinline__ void fisher_yates(const SweepArgs &a, uint32_t grep, int n, int t, int32_t *sv,
+                                             int32_t *sp, int bar) {
+    constexpr int G = 32 * WPR;
+    for (int q = t; 4 * q < n; q += G) {
+        const uint4 o = philox4x32_10(a.inst, grep, 0xFFFFFFFFu, (uint32_t)q, a.key0, a.key1);
+        reinterpret_cast<uint4 *>(sv)[q] = o;
+    }
+    for (int m = t; m < n; m += G) sp[m] = m;
+    group_sync<WPR>(bar);
+    if (t == 0) {
+        for (int k = n - 1; k >= 1; --k) {
+            const int j = (int)__umulhi((uint32_t)sv[k], (uint32_t)(k + 1));
+            const int x = sp[k];
+            sp[k] = sp[j];
+            sp[j] = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 5 draw over the n outcomes whose swap energies the group has written to
+// sv[0..n) (lmin: the minimum over this thread's own candidates): group
+// minimum, binary32 weights of the shifted energies, thread-contiguous 64-bit
+// prefix sums (thread t holds outcomes t*MAXK .. t*MAXK + MAXK - 1), the
+// 64-bit draw scaled by the total, and the first outcome whose inclusive
+// prefix sum exceeds it. Returns (chosen location js, its energy change,
+// sp[js]), the same on every thread of the group; sp[js] is read by the
+// owning thread before the final synchronisation, so the caller may rewrite
+// sp once every thread has returned. Ends with the group synchronised, so sv
+// may be rewritten afterwards.
+// ---------------------------------------------------------------------------
+template <int MAXK, int WPR>
+__device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, int n, int t, int lmin,
+                                         float beta, unsigned long long draw, int bar, GroupScratch *gs) {
+    const int lane = t & 31;
+    const int wg = t >> 5;
+    int dmin = __reduce_min_sync(kFull, lmin);
+    if constexpr (WPR > 1) {
+        if (lane == 0) gs->wmin[wg] = dmin;
+        group_sync<WPR>(bar);
+        dmin = gs->wmin[0];
+#pragma unroll
+        for (int w = 1; w < WPR; ++w) dmin = min(dmin, gs->wmin[w]);
+    } else {
+        __syncwarp();
+    }
+
+    // ---- sample: thread-contiguous weights, 64-bit prefix sums
+    int dc[MAXK];
+    load_block<MAXK>(sv, t, dc);
+    unsigned long long pre[MAXK];
+    unsigned long long lsum = 0;
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k) {
+        if (t * MAXK + k < n) lsum += eq5_weight(dc[k] - dmin, beta);
+        pre[k] = lsum;
+    }
+    unsigned long long incl = lsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    unsigned long long total = __shfl_sync(kFull, incl, 31);
+    if constexpr (WPR > 1) {
+        if (lane == 31) gs->wtot[wg] = incl;
+        group_sync<WPR>(bar);
+        // every thread reads all warp totals (broadcast) and sums the
+        // ones before its warp
+        unsigned long long off = 0;
+        total = 0;
+#pragma unroll
+        for (int w = 0; w < WPR; ++w) {
+            const unsigned long long v = gs->wtot[w];
+            off += w < wg ? v : 0ull;
+            total += v;
+        }
+        incl += off;
+    }
+    const unsigned long long excl = incl - lsum;
+    const unsigned long long tdraw = __umul64hi(draw, total);
+    const bool own = (tdraw >= excl) && (tdraw < incl);
+    int jloc = 0, dsel = 0, fsel = 0;
+    if (own) {
+        int kk = MAXK - 1;
+#pragma unroll
+        for (int k = MAXK - 1; k >= 0; --k)
+            if (excl + pre[k] > tdraw) kk = k;
+#pragma unroll
+        for (int k = 0; k < MAXK; ++k)
+            if (k == kk) dsel = dc[k];
+        jloc = t * MAXK + kk;
+        fsel = sp[jloc];
+    }
+    int js, dstar, fb;
+    if constexpr (WPR > 1) {
+        if (own) {
+            gs->sel_j = jloc;
+            gs->sel_d = dsel;
+            gs->sel_f = fsel;
+        }
+        group_sync<WPR>(bar);
+        js = gs->sel_j;
+        dstar = gs->sel_d;
+        fb = gs->sel_f;
+    } else {
+        const int src = __ffs(__ballot_sync(kFull, own)) - 1;
+        js = __shfl_sync(kFull, jloc, src);
+        dstar = __shfl_sync(kFull, dsel, src);
+        fb = __shfl_sync(kFull, fsel, src);
+        __syncwarp();
+    }
+    return make_int3(js, dstar, fb);
+}
+
 __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
     x.x += u * v.x;
     x.y += u * v.y;
@@ -252,24 +376,9 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     int32_t *gp = a.perm + (size_t)r * n;
     int32_t *gbp = a.best_perm + (size_t)r * n;
 
-    // ---- permutation: Fisher-Yates from the last position down; step k uses
-    // word k%4 of Philox(inst, replica, 0xFFFFFFFF, k/4) and index
-    // floor(u (k+1) / 2^32).
+    // ---- permutation
     if (a.fresh) {
-        for (int q = t; 4 * q < n; q += G) {
-            const uint4 o = philox4x32_10(a.inst, grep, 0xFFFFFFFFu, (uint32_t)q, a.key0, a.key1);
-            reinterpret_cast<uint4 *>(sv)[q] = o;
-        }
-        for (int m = t; m < n; m += G) sp[m] = m;
-        group_sync<WPR>(bar);
-        if (t == 0) {
-            for (int k = n - 1; k >= 1; --k) {
-                const int j = (int)__umulhi((uint32_t)sv[k], (uint32_t)(k + 1));
-                const int x = sp[k];
-                sp[k] = sp[j];
-                sp[j] = x;
-            }
-        }
+        fisher_yates<WPR>(a, grep, n, t, sv, sp, bar);
     } else {
         for (int m = t; m < n; m += G) sp[m] = gp[m];
     }
@@ -394,8 +503,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     }
                 }
             }
-            return;
-        }
+        } else {
         int uw[ROWS];
 #pragma unroll
         for (int k = 0; k < ROWS; ++k) {
@@ -416,6 +524,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     *row = x;
                 }
             }
+        }
         }
     };
 
@@ -833,80 +942,12 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         lmin = min(lmin, d);
                     }
                 }
-                int dmin = __reduce_min_sync(kFull, lmin);
-                if constexpr (WPR > 1) {
-                    if (lane == 0) gs->wmin[wg] = dmin;
-                    group_sync<WPR>(bar);
-                    dmin = gs->wmin[0];
-#pragma unroll
-                    for (int w = 1; w < WPR; ++w) dmin = min(dmin, gs->wmin[w]);
-                } else {
-                    __syncwarp();
-                }
-
-                // ---- sample: thread-contiguous weights, 64-bit prefix sums
-                int dc[MAXK];
-                load_block<MAXK>(sv, t, dc);
-                unsigned long long pre[MAXK];
-                unsigned long long lsum = 0;
-#pragma unroll
-                for (int k = 0; k < MAXK; ++k) {
-                    if (t * MAXK + k < n) lsum += eq5_weight(dc[k] - dmin, beta);
-                    pre[k] = lsum;
-                }
-                unsigned long long incl = lsum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned long long y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                unsigned long long total = __shfl_sync(kFull, incl, 31);
-                if constexpr (WPR > 1) {
-                    if (lane == 31) gs->wtot[wg] = incl;
-                    group_sync<WPR>(bar);
-                    // every thread reads all warp totals (broadcast) and sums the
-                    // ones before its warp
-                    unsigned long long off = 0;
-                    total = 0;
-#pragma unroll
-                    for (int w = 0; w < WPR; ++w) {
-                        const unsigned long long v = gs->wtot[w];
-                        off += w < wg ? v : 0ull;
-                        total += v;
-                    }
-                    incl += off;
-                }
-                const unsigned long long excl = incl - lsum;
-                const unsigned long long tdraw = __umul64hi(draw, total);
-                const bool own = (tdraw >= excl) && (tdraw < incl);
-                int jloc = 0, dsel = 0;
-                if (own) {
-                    int kk = MAXK - 1;
-#pragma unroll
-                    for (int k = MAXK - 1; k >= 0; --k)
-                        if (excl + pre[k] > tdraw) kk = k;
-#pragma unroll
-                    for (int k = 0; k < MAXK; ++k)
-                        if (k == kk) dsel = dc[k];
-                    jloc = t * MAXK + kk;
-                }
-                int js, dstar;
-                if constexpr (WPR > 1) {
-                    if (own) *reinterpret_cast<int2 *>(&gs->sel_j) = make_int2(jloc, dsel);
-                    group_sync<WPR>(bar);
-                    const int2 sel = *reinterpret_cast<const int2 *>(&gs->sel_j);
-                    js = sel.x;
-                    dstar = sel.y;
-                } else {
-                    const int src = __ffs(__ballot_sync(kFull, own)) - 1;
-                    js = __shfl_sync(kFull, jloc, src);
-                    dstar = __shfl_sync(kFull, dsel, src);
-                    __syncwarp();
-                }
+                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, beta, draw, bar, gs);
+                const int js = sel.x, dstar = sel.y;
                 if (js == i) continue;
 
                 // ---- apply the swap i <-> js
-                const int fb = sp[js];
+                const int fb = sel.z;  // sp[js], read before thread 0 rewrites it
                 // current I[i][fb] and I[js][fa], for the two p-diagonal entries that move
                 int tib = 0, tja = 0;
                 if (t == 0) {
@@ -1183,5 +1224,16 @@ int batch_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *descs, 
         return batch_one<MK, W, TS, K>(d, u, nu, q, grid, threads, smem, st, blocks, query);
 
 #define PDIT_SWEEP_SHAPES_ALL(X) PDIT_SWEEP_SHAPES_COMMON(X) PDIT_SWEEP_SHAPES_DEFERRED(X)
+
+// Flow-class sweep kernels (pdit_class.cu): one per storage type of D and
+// per (MAXK, WPR) with 32 * WPR * MAXK in {32, 64, 128, 256}. Return a
+// cudaError_t value; cudaErrorInvalidValue for a shape with no kernel.
+template <typename DT>
+int class_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks);
+template <typename DT>
+int class_launch(int maxk, int wpr, const SweepArgs &a, int grid, int threads, size_t smem, cudaStream_t stream);
+__host__ __device__ constexpr int class_bound(int maxk, int wpr) {
+    return maxk >= 4 ? 512 : 1024;
+}
 
 }  // namespace pdit

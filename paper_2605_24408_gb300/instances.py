@@ -133,6 +133,11 @@ def named(name: str, seed: int = 0):
     'n12'  : 3x4 grid, flow density 0.5 (with 'n9', its 3x3 brute-force sibling)
     'n30'  : 5x6 grid, flow density 0.4
     'n100' : dense 0..99
+    'n100a': the general-form analogue of 'n100': every entry of D and F
+             drawn independently, uniform 0..99, zero diagonals (asymmetric)
+    'c256' : two-level flow at the size of the paper's tai256c: N = 256, flow
+             1 between every pair of a 92-facility subset and 0 elsewhere, D
+             dense symmetric uniform 1..99 (synthetic values)
     """
     if name == "n12":
         return grid_instance(3, 4, 0.5, seed)
@@ -142,6 +147,10 @@ def named(name: str, seed: int = 0):
         return grid_instance(5, 6, 0.4, seed)
     if name == "n100":
         return dense_instance(100, seed)
+    if name == "n100a":
+        return asymmetric(100, 0, 99, seed, 101), asymmetric(100, 0, 99, seed, 103)
+    if name == "c256":
+        return flow_class_instance(256, 92, seed)
     raise KeyError(name)
 
 
@@ -175,6 +184,22 @@ def asymmetric_instance(n: int, seed: int, diag: bool = False):
     else:
         D[np.arange(n), np.arange(n)] = 0
     return D.astype(np.int32), F
+
+
+def flow_class_instance(n: int, k: int, seed: int, lo: int = 1, hi: int = 99, f0: int = 0, f: int = 1,
+                        fdiag: int = 0):
+    """A two-level-flow instance (the structure of the paper's tai256c
+    discussion, synthetic values): D dense symmetric, off-diagonal uniform
+    lo..hi, zero diagonal; a subset K of k facilities (the k smallest hashes of
+    the facility ids, so not the first k); F[c][d] = f0 + f when c and d are
+    both in K, f0 otherwise (c != d), and fdiag on the diagonal."""
+    D = dense_symmetric(n, lo, hi, seed, tag=111)
+    order = np.argsort(hash_u64(seed, 113, np.arange(n, dtype=np.uint64)), kind="stable")
+    x = np.zeros(n, dtype=np.int64)
+    x[order[:k]] = 1
+    F = f0 + f * np.outer(x, x)
+    F[np.arange(n), np.arange(n)] = fdiag
+    return D, F.astype(np.int32)
 
 
 def request_instance(request_id: int, lo: int = 20, hi: int = 200):

@@ -26,6 +26,9 @@ PDIT_ECUDA = -4
 PDIT_EDEVICE = -5
 PDIT_ENOTSUP = -6
 PDIT_EIO = -7
+PDIT_FORM_SYMMETRIC = 0
+PDIT_FORM_GENERAL = 1
+PDIT_FORM_FLOW_CLASSES = 2
 PDIT_N_MAX = 256
 PDIT_MODE_ANNEAL = 0
 PDIT_MODE_PT = 1
@@ -165,6 +168,10 @@ def lib():
     L.pdit_server_result.restype = ctypes.c_int
     L.pdit_server_destroy.argtypes = [vp]
     L.pdit_server_destroy.restype = None
+    L.pdit_instance_form.argtypes = [vp]
+    L.pdit_instance_form.restype = ctypes.c_int
+    L.pdit_set_class_update.argtypes = [vp, ctypes.c_int]
+    L.pdit_set_class_update.restype = ctypes.c_int
     L.pdit_read_qaplib.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), vp, vp, ctypes.c_size_t]
     L.pdit_read_qaplib.restype = ctypes.c_int
     L.pdit_read_qaplib_solution.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
@@ -292,6 +299,17 @@ def write_qaplib_solution(path: str, perm, cost: int):
     perm = np.ascontiguousarray(perm, np.int32)
     _check(lib().pdit_write_qaplib_solution(os.fsencode(path), perm.size, int(cost), _ptr(perm)),
            "pdit_write_qaplib_solution")
+
+
+def pdit_instance_form(q: Qap) -> int:
+    rc = lib().pdit_instance_form(q.handle)
+    if rc < 0:
+        raise PditError(rc, "pdit_instance_form")
+    return rc
+
+
+def pdit_set_class_update(q: Qap, enable: bool):
+    _check(lib().pdit_set_class_update(q.handle, 1 if enable else 0), "pdit_set_class_update")
 
 
 def pdit_set_warps_per_replica(q: Qap, wpr: int):
