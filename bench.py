@@ -43,10 +43,12 @@ WORKLOADS = {
     "n12": ("n12", 64, 1000, "linear"),
     "n100a": ("n100a", 4096, 10000, "linear"),
     "c256": ("c256", 4096, 2000, "linear"),
+    "n256": ("n256", 2048, 1000, "linear"),
 }
 WORKLOAD_TEXT = {
     "n100": "dense symmetric QAP N=100 (D, F uniform 0..99)",
     "n100a": "dense asymmetric QAP N=100 (every entry of D and F independent uniform 0..99, zero diagonals)",
+    "n256": "dense symmetric QAP N=256 (D, F uniform 0..99): influence tables in global memory",
     "c256": "two-level flow N=256 (flow 1 between every pair of a 92-facility subset, 0 elsewhere; "
             "D dense symmetric uniform 1..99): the structure of the paper's tai256c, synthetic values",
 }
@@ -91,11 +93,11 @@ def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pend
       accepted swap: read+write of the N x N int32 table (8 N^2), two D rows
       and two F rows (4 N dt), the column factor written once (4 N), the
       p-diagonal read and written (8 N).
-    Deferred updates (pending = 4): the gather also reads the packed factors
-    u[j], v[p(j)] (+8 N); an accepted swap writes one byte of each packed
-    factor per entry (2 N), reads two D rows and two F rows (4 N dt) and p,
-    h (12 N), and a quarter of a table rewrite with its packed factors
-    (2 N^2 + 2 N).
+    Deferred updates (pending = 4 or 16 terms, pending / 4 packed words):
+    the gather also reads the packed factors u[j], v[p(j)] (+8 N per word);
+    an accepted swap writes one byte of each packed factor per entry (2 N),
+    reads two D rows and two F rows (4 N dt) and p, h (12 N), and 1 / pending
+    of a table rewrite (8 N^2 / pending).
     General form: the gather also reads D[j][i] and F[p(j)][p(i)] (+2 N dt);
     a swap reads D and F columns as well (+4 N dt) and carries two rank-1
     terms (two factor vectors; two of the four pending slots, so half a table
@@ -107,11 +109,12 @@ def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pend
             gather += 2 * n * dt_bytes
             swap += 4 * n * dt_bytes + 4 * n
     else:
-        gather = 24 * n + 2 * n * dt_bytes
-        swap = 2 * n * n + 4 * n * dt_bytes + 16 * n
+        words = pending // 4  # packed words per entry, read by both queries
+        gather = 16 * n + 8 * n * words + 2 * n * dt_bytes
+        swap = 8 * n * n / pending + 4 * n * dt_bytes + 16 * n
         if general:
             gather += 2 * n * dt_bytes
-            swap += 2 * n * n + 4 * n * dt_bytes + 4 * n
+            swap += 8 * n * n / pending + 4 * n * dt_bytes + 4 * n
     return gather + accept_frac * swap
 
 

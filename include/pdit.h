@@ -115,7 +115,8 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
  * would use: shape[0] warps per replica, [1] candidates per thread, [2]
  * replicas per CTA, [3] CTAs, [4] 1 if the influence tables live in shared
  * memory (0: global memory), [5] dynamic shared memory bytes per CTA.
- * [6] swaps held before the influence table is rewritten (1 = after each).
+ * [6] pending rank-1 terms held before the influence table is rewritten (1 =
+ * after each swap; 4 or 16).
  * `shape` is a host array of 7 ints. Errors: PDIT_EINVAL, PDIT_ENOTSUP.
  */
 int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape);
@@ -151,12 +152,16 @@ int pdit_set_class_update(pdit_qap *h, int enable);
 /*
  * pdit_set_pending_swaps -- table-update batching of later calls on this
  * handle: k = 1 rewrites the influence table after every accepted swap
- * (the rank-1 update implied by Eq. 2); k = 4 keeps up to four accepted
- * swaps as pending rank-1 terms that every query adds in, and rewrites the
- * table once per four swaps (a rank-4 update). 0 restores the built-in
- * choice. k = 4 needs max - min <= 127 over the entries of D and of F (so
- * every swap factor fits a signed byte) (PDIT_ENOTSUP otherwise, at the next
- * call). Results do not depend on k.
+ * (the rank-1 update implied by Eq. 2); k = 4 keeps up to four pending
+ * rank-1 terms (four accepted swaps; two in the general form) that every
+ * query adds in, and rewrites the table once they are full (a rank-4
+ * update); k = 16 does the same with sixteen terms and is available when
+ * the tables live in global memory (n above about 190). 0 restores the
+ * built-in choice (16 for global tables, else 4 when it costs no resident
+ * replica, else 1). k > 1 needs max - min <= 127 over the entries of D and
+ * of F (so every swap factor fits a signed byte); PDIT_ENOTSUP otherwise,
+ * or for k = 16 with tables in shared memory, at the next call. Results do
+ * not depend on k.
  * Errors: PDIT_EINVAL.
  */
 int pdit_set_pending_swaps(pdit_qap *h, int k);

@@ -90,7 +90,7 @@ int stage_stride(int n, int dt) {
 struct Plan {
     int maxk = 1, wpr = 1, pk = 1;
     bool tsmem = true, cls = false;
-    int stride = 0, sv_len = 0, cupim_off = 0, v2_off = 0, dstride = 0;
+    int stride = 0, sv_len = 0, cupim_off = 0, v2_off = 0, rc_off = 0, dstride = 0;
     size_t table_elems = 0;  // int32 entries of one replica's saved table (workspace)
     size_t df_bytes = 0, group_bytes = 0, smem = 0;
     int groups = 1, threads = 32, grid = 1;
@@ -131,7 +131,7 @@ size_t group_bytes_for(int n, int stride, int cover, bool tsmem, int pk, int ext
     const size_t npad = (size_t)((n + 3) & ~3);
     const size_t vec = 4 * (2 * npad + (size_t)sv_len_for(stride, cover) + (size_t)extra_sv);
     const size_t table = tsmem ? (size_t)4 * n * stride : 0;
-    const size_t ring = pk > 1 ? (size_t)8 * npad : 0;  // packed u and v words
+    const size_t ring = pk > 1 ? (size_t)8 * npad * (pk / 4) : 0;  // packed u and v words
     return align_up(pdit::kScratchBytes + table + vec + ring, 16);
 }
 
@@ -145,31 +145,42 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     p->stride = table_stride(n);
     const int base = sv_len_for(p->stride, cover);
     // Extra scratch-vector entries for `k` pending terms: the column factor
-    // of the general form's immediate rank-2 update, and the proposal,
-    // energy-change and order arrays of concurrent updates.
-    auto extra_for = [&](int k) { return (h->asym && k == 1 ? npad : 0) + (cupim ? 3 * npad : 0); };
+    // of the general form's immediate rank-2 update, the gathered table
+    // values (tables in global memory), and the proposal, energy-change and
+    // order arrays of concurrent updates.
+    auto extra_for = [&](int k) {
+        return (h->asym && k == 1 ? npad : 0) + (p->tsmem ? 0 : 2 * npad) + (cupim ? 3 * npad : 0);
+    };
     p->dstride = h->asym ? stage_stride(n, h->dt_bytes) : n;
     p->df_bytes = align_up((size_t)2 * n * p->dstride * h->dt_bytes, 16);
     const size_t budget = h->smem_optin - reserve;
+    p->tsmem = true;
     p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1, extra_for(1)) <= budget;
     if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;
     const bool defer_ok = h->packed_ok != 0;
-    if (pk != 0 && pk != 1 && pk != 4) return PDIT_EINVAL;
-    if (pk == 4 && !defer_ok) return PDIT_ENOTSUP;
+    if (pk != 0 && pk != 1 && pk != 4 && pk != 16) return PDIT_EINVAL;
+    if (pk > 1 && !defer_ok) return PDIT_ENOTSUP;
+    if (pk == 16 && p->tsmem) return PDIT_ENOTSUP;  // compiled for global tables only
     if (pk == 0) {
         // Defer table rewrites when the packed factors cost no replica slot
-        // (tables in shared memory), and always for tables in global memory.
+        // (tables in shared memory: 4 pending terms), and always for tables
+        // in global memory (16 pending terms: each rewrite streams the whole
+        // table through L2).
         pk = 1;
         if (defer_ok) {
             const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1, extra_for(1));
             const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4, extra_for(4));
-            if (!p->tsmem || (budget - p->df_bytes) / g4 >= (budget - p->df_bytes) / g1) pk = 4;
+            if (!p->tsmem)
+                pk = 16;
+            else if ((budget - p->df_bytes) / g4 >= (budget - p->df_bytes) / g1)
+                pk = 4;
         }
     }
     p->pk = pk;
     p->table_elems = (size_t)n * p->stride;
     p->v2_off = base;
-    p->cupim_off = base + (h->asym && pk == 1 ? npad : 0);
+    p->rc_off = base + (h->asym && pk == 1 ? npad : 0);
+    p->cupim_off = p->rc_off + (p->tsmem ? 0 : 2 * npad);
     p->sv_len = base + extra_for(pk);
     p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk, extra_for(pk));
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
@@ -315,6 +326,7 @@ void fill_shape(pdit::SweepArgs &a, const pdit_qap *h, const Plan &p) {
     a.sv_len = p.sv_len;
     a.cupim_off = p.cupim_off;
     a.v2_off = p.v2_off;
+    a.rc_off = p.rc_off;
     a.groups = p.groups;
     a.cls_x = h->dx;
     a.cls_f = h->cls_f;
@@ -641,7 +653,7 @@ int pdit_set_class_update(pdit_qap *h, int enable) {
 }
 
 int pdit_set_pending_swaps(pdit_qap *h, int k) {
-    if (!h || (k != 0 && k != 1 && k != 4)) return PDIT_EINVAL;
+    if (!h || (k != 0 && k != 1 && k != 4 && k != 16)) return PDIT_EINVAL;
     h->force_pk = k;
     return PDIT_OK;
 }
@@ -863,7 +875,7 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     int best_wpr = 0, best_pk = 0, rc = PDIT_OK;
     float best_ms = 0.0f;
     for (int wpr = 1; wpr <= cover / 32 && wpr <= 8 && e == cudaSuccess && rc == PDIT_OK; wpr <<= 1)
-        for (int pk = 1; pk <= 4 && e == cudaSuccess && rc == PDIT_OK; pk += 3) {
+        for (int pk = 1; pk <= 16 && e == cudaSuccess && rc == PDIT_OK; pk *= 4) {
             const bool cls = h->cls && h->use_cls;
             if (cls && pk != 1) continue;  // the flow-class kernel keeps no table
             h->force_wpr = wpr;

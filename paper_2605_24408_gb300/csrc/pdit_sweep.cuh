@@ -54,6 +54,7 @@ struct SweepArgs {
                            // 3 concurrent updates (beta[s])
     int cupim_off;         // mode 3: offset (int32 entries) of the proposal arrays in the scratch vector
     int v2_off;            // general form, immediate updates: offset of the second column factor
+    int rc_off;            // global tables: offset of the gathered table values (row, then column)
     // flow classes (pdit_class.cu): F[c][d] = f0 + f x_c x_d off the diagonal
     const uint8_t *cls_x;  // x_c of every facility
     int cls_f;             // f
@@ -336,6 +337,12 @@ __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, i
     return make_int3(js, dstar, fb);
 }
 
+// Bytes of packed word w that hold one of the np pending terms (4 per word).
+__device__ __forceinline__ uint32_t pending_mask(int np, int w) {
+    const int v = np - 4 * w;
+    return v >= 4 ? 0xFFFFFFFFu : (v <= 0 ? 0u : ((1u << (8 * v)) - 1u));
+}
+
 __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
     x.x += u * v.x;
     x.y += u * v.y;
@@ -366,6 +373,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     // warp touches 512 contiguous bytes per access; each lane keeps the
     // column factors of its quads lane, lane + 32, ... in registers.
     constexpr int QL = (ROWS + 3) / 4;     // quads per lane along a row (cover / 128)
+    constexpr int PW = PK > 1 ? PK / 4 : 1;  // packed words per entry (4 pending terms each)
     const int lane = t & 31;
     const int wg = t >> 5;
     const int n = a.n;
@@ -463,14 +471,18 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     // for the np <= 4 accepted swaps (i_q <-> j_q, facilities a_q, b_q) since
     // the last rewrite of T (general form: two terms per swap, the column
     // term u[m] = D[m][i_q] - D[m][j_q], v[c] = F[c][b_q] - F[c][a_q] and the
-    // row term above, so T is rewritten every two swaps). upk[m] packs u_0..u_3[m] and vpk[c] packs
-    // v_0..v_3[c] as signed bytes (exact: every |u|, |v| <= 127 for the
-    // instances this path is chosen for), so one dp4a adds all pending terms
-    // of an entry; bytes q >= np are masked off. T is rewritten once per four
-    // swaps. Exact integers throughout.
+    // row term above, so T is rewritten every two swaps). Word w of upk
+    // (upk[w * Npad + m]) packs u_{4w}..u_{4w+3}[m] and word w of vpk packs
+    // v_{4w}..v_{4w+3}[c] as signed bytes (exact: every |u|, |v| <= 127 for the
+    // instances this path is chosen for), so one dp4a per word adds the
+    // pending terms of an entry; bytes q >= np are masked off. PK = 4 (one
+    // word) for tables in shared memory; PK = 16 (four words) for tables in
+    // global memory, where every rewrite streams the whole table through L2.
+    // Exact integers throughout.
     int np = 0;
+    bool flushed = false;  // the last apply_swap rewrote the table
     if constexpr (PK > 1) {
-        for (int c = t; c < npad; c += G) {
+        for (int c = t; c < PW * npad; c += G) {
             upk[c] = 0u;
             vpk[c] = 0u;
         }
@@ -478,53 +490,75 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
 
     // T += sum_{q < np} u_q (x) v_q on this thread's (rows, column quads).
     auto flush = [&]() {
-        const uint32_t mask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
-        if constexpr (TG) {
-            int4 vq[QL];
+        uint32_t mk[PW];
 #pragma unroll
-            for (int c2 = 0; c2 < QL; ++c2) {
-                const int cq = lane + 32 * c2;
-                vq[c2] = cq < nq ? reinterpret_cast<const int4 *>(vpk)[cq] : make_int4(0, 0, 0, 0);
+        for (int w = 0; w < PW; ++w) mk[w] = pending_mask(np, w);
+        const int4 *v4 = reinterpret_cast<const int4 *>(vpk);
+        if constexpr (TG) {
+            // lanes along a row: a warp touches 512 contiguous bytes per access
+            int4 vq[PW == 1 ? QL : 1];
+            if constexpr (PW == 1) {
+#pragma unroll
+                for (int c2 = 0; c2 < QL; ++c2) {
+                    const int cq = lane + 32 * c2;
+                    vq[c2] = cq < nq ? v4[cq] : make_int4(0, 0, 0, 0);
+                }
             }
 #pragma unroll 2
             for (int m = wg; m < n; m += WPR) {
-                const int um = (int)(upk[m] & mask);
+                int um[PW];
+#pragma unroll
+                for (int w = 0; w < PW; ++w) um[w] = (int)(upk[w * npad + m] & mk[w]);
                 int4 *row = reinterpret_cast<int4 *>(T + m * S);
 #pragma unroll
                 for (int c2 = 0; c2 < QL; ++c2) {
                     const int cq = lane + 32 * c2;
                     if (cq < nq) {
                         int4 x = row[cq];
-                        x.x = __dp4a(um, vq[c2].x, x.x);
-                        x.y = __dp4a(um, vq[c2].y, x.y);
-                        x.z = __dp4a(um, vq[c2].z, x.z);
-                        x.w = __dp4a(um, vq[c2].w, x.w);
+#pragma unroll
+                        for (int w = 0; w < PW; ++w) {
+                            int4 v;
+                            if constexpr (PW == 1)
+                                v = vq[c2];
+                            else
+                                v = v4[w * nq + cq];
+                            x.x = __dp4a(um[w], v.x, x.x);
+                            x.y = __dp4a(um[w], v.y, x.y);
+                            x.z = __dp4a(um[w], v.z, x.z);
+                            x.w = __dp4a(um[w], v.w, x.w);
+                        }
                         row[cq] = x;
                     }
                 }
             }
         } else {
-        int uw[ROWS];
-#pragma unroll
-        for (int k = 0; k < ROWS; ++k) {
-            const int m = lane + 32 * k;
-            uw[k] = m < n ? (int)(upk[m] & mask) : 0;
-        }
-        for (int cq = wg; cq < nq; cq += WPR) {
-            const int4 vq = reinterpret_cast<const int4 *>(vpk)[cq];
+            int uw[ROWS][PW];
 #pragma unroll
             for (int k = 0; k < ROWS; ++k) {
-                if (lane + 32 * k < n) {
-                    int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
-                    int4 x = *row;
-                    x.x = __dp4a(uw[k], vq.x, x.x);
-                    x.y = __dp4a(uw[k], vq.y, x.y);
-                    x.z = __dp4a(uw[k], vq.z, x.z);
-                    x.w = __dp4a(uw[k], vq.w, x.w);
-                    *row = x;
+                const int m = lane + 32 * k;
+#pragma unroll
+                for (int w = 0; w < PW; ++w) uw[k][w] = m < n ? (int)(upk[w * npad + m] & mk[w]) : 0;
+            }
+            for (int cq = wg; cq < nq; cq += WPR) {
+                int4 vq[PW];
+#pragma unroll
+                for (int w = 0; w < PW; ++w) vq[w] = v4[w * nq + cq];
+#pragma unroll
+                for (int k = 0; k < ROWS; ++k) {
+                    if (lane + 32 * k < n) {
+                        int4 *row = reinterpret_cast<int4 *>(T + (lane + 32 * k) * S) + cq;
+                        int4 x = *row;
+#pragma unroll
+                        for (int w = 0; w < PW; ++w) {
+                            x.x = __dp4a(uw[k][w], vq[w].x, x.x);
+                            x.y = __dp4a(uw[k][w], vq[w].y, x.y);
+                            x.z = __dp4a(uw[k][w], vq[w].z, x.z);
+                            x.w = __dp4a(uw[k][w], vq[w].w, x.w);
+                        }
+                        *row = x;
+                    }
                 }
             }
-        }
         }
     };
 
@@ -629,10 +663,11 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             }
             }
         } else {
-            // Deferred: record u and v of this swap in byte np of upk, vpk
-            // (general form: the column term in byte np, the row term in np + 1).
-            int8_t *ub = reinterpret_cast<int8_t *>(upk) + np;
-            int8_t *vb = reinterpret_cast<int8_t *>(vpk) + np;
+            // Deferred: record u and v of this swap in slot np of upk, vpk
+            // (general form: the column term in slot np, the row term in np + 1,
+            // the same word since np is even then).
+            int8_t *ub = reinterpret_cast<int8_t *>(upk + (np >> 2) * npad) + (np & 3);
+            int8_t *vb = reinterpret_cast<int8_t *>(vpk + (np >> 2) * npad) + (np & 3);
             for (int c = t; c < npad; c += G) {
                 if constexpr (ASYM) {
                     ub[4 * c] = (int8_t)(c < n ? (int)sD[c * dn + i] - (int)sD[c * dn + js] : 0);
@@ -672,6 +707,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
         }
         if constexpr (PK > 1) {
             np += ASYM ? 2 : 1;
+            flushed = np == PK;
             if (np == PK) {
                 group_sync<WPR>(bar);  // packed factors and thread 0's table reads complete
                 flush();
@@ -679,6 +715,33 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             }
         }
     };
+
+    // Tables in global memory: the gathers of the next update (its row
+    // T[l][p(j)] and column T[j][p(l)] for this thread's candidates) are
+    // loaded one update ahead, so their latency overlaps the current update.
+    // Between rewrites the global table does not change (pending terms are
+    // added from shared memory when the values are used), so a prefetch
+    // stays valid unless the table was rewritten or the swap changed p(l) or
+    // a candidate's p(j); those cases are reloaded after the swap.
+    int pre_row[TG ? MAXK : 1], pre_col[TG ? MAXK : 1];
+    auto prefetch = [&](int l) {
+        if constexpr (TG) {
+            const int pl = sp[l];
+#pragma unroll
+            for (int k = 0; k < MAXK; ++k) {
+                const int j = t + G * k;
+                if (j < n) {
+                    pre_row[k] = T[l * S + sp[j]];
+                    pre_col[k] = T[j * S + pl];
+                }
+            }
+        }
+    };
+    int32_t *srow = sv + a.rc_off;  // TG: gathered row values T[i][p(j)] by j, then the column values
+    int32_t *scol = srow + npad;
+    if constexpr (TG) {
+        if (a.mode != 3 && a.sweep_begin < a.sweep_end) prefetch(0);
+    }
 
     for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
         if (a.stop) {
@@ -698,7 +761,9 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             int32_t *pj = sv + a.cupim_off;  // proposal of each location
             int32_t *pd = pj + npad;          // its snapshot energy change; later: taken flags
             int32_t *ord = pd + npad;         // movers in priority order; then the accepted ones
-            const uint32_t pmask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
+            uint32_t pm[PW];
+#pragma unroll
+            for (int w = 0; w < PW; ++w) pm[w] = pending_mask(np, w);
             // A. warp wg draws the proposals of locations wg, wg + WPR, ...
             for (int ib = wg; ib < n; ib += 32 * WPR) {
                 const int myrow = ib + WPR * lane;
@@ -713,10 +778,13 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     const int hi = sh[i];
                     const DT *Di = sD + i * dn;
                     const DT *Fa = sF + fa * dn;
-                    int ui4 = 0, vfa4 = 0;
+                    int ui[PW], vfa[PW];
                     if constexpr (PK > 1) {
-                        ui4 = (int)(upk[i] & pmask);
-                        vfa4 = (int)vpk[fa];
+#pragma unroll
+                        for (int w = 0; w < PW; ++w) {
+                            ui[w] = (int)(upk[w * npad + i] & pm[w]);
+                            vfa[w] = (int)vpk[w * npad + fa];
+                        }
                     }
                     int dv[ROWS];
                     int lmin = 0x7FFFFFFF;
@@ -731,8 +799,11 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                             int row_ib = T[i * S + b];
                             int col_ja = T[j * S + fa];
                             if constexpr (PK > 1) {
-                                row_ib = __dp4a(ui4, (int)vpk[b], row_ib);
-                                col_ja = __dp4a((int)(upk[j] & pmask), vfa4, col_ja);
+#pragma unroll
+                                for (int w = 0; w < PW; ++w) {
+                                    row_ib = __dp4a(ui[w], (int)vpk[w * npad + b], row_ib);
+                                    col_ja = __dp4a((int)(upk[w * npad + j] & pm[w]), vfa[w], col_ja);
+                                }
                             }
                             if constexpr (ASYM) {
                                 const int dji = sD[j * dn + i];
@@ -835,12 +906,15 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 const int js = pj[i];
                 const int fa = sp[i], fb = sp[js];
                 if (t == 0) {
-                    const uint32_t m4 = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
                     int rowv = T[i * S + fb];
                     int colv = T[js * S + fa];
                     if constexpr (PK > 1) {
-                        rowv = __dp4a((int)(upk[i] & m4), (int)vpk[fb], rowv);
-                        colv = __dp4a((int)(upk[js] & m4), (int)vpk[fa], colv);
+#pragma unroll
+                        for (int w = 0; w < PW; ++w) {
+                            const uint32_t m4 = pending_mask(np, w);
+                            rowv = __dp4a((int)(upk[w * npad + i] & m4), (int)vpk[w * npad + fb], rowv);
+                            colv = __dp4a((int)(upk[w * npad + js] & m4), (int)vpk[w * npad + fa], colv);
+                        }
                     }
                     const int dij = sD[i * dn + js];
                     const int fab = sF[fa * dn + fb];
@@ -897,11 +971,15 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 const DT *Di = sD + i * dn;
                 const DT *Fa = sF + fa * dn;
                 // pending factors at this location: packed u_q[i] and v_q[fa]
-                const uint32_t pmask = np >= 4 ? 0xFFFFFFFFu : ((1u << (8 * np)) - 1u);
-                int ui4 = 0, vfa4 = 0;
+                uint32_t pm[PW];
+                int ui[PW], vfa[PW];
                 if constexpr (PK > 1) {
-                    ui4 = (int)(upk[i] & pmask);
-                    vfa4 = (int)vpk[fa];
+#pragma unroll
+                    for (int w = 0; w < PW; ++w) {
+                        pm[w] = pending_mask(np, w);
+                        ui[w] = (int)(upk[w * npad + i] & pm[w]);
+                        vfa[w] = (int)vpk[w * npad + fa];
+                    }
                 }
 
                 // ---- gather: Eq. 3 for every candidate j
@@ -913,11 +991,24 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         const int b = sp[j];
                         const int dij = Di[j];
                         const int fab = Fa[b];
-                        int row_ib = T[i * S + b];
-                        int col_ja = T[j * S + fa];
+                        int row_ib, col_ja;
+                        if constexpr (TG) {
+                            row_ib = pre_row[k];
+                            col_ja = pre_col[k];
+                        } else {
+                            row_ib = T[i * S + b];
+                            col_ja = T[j * S + fa];
+                        }
                         if constexpr (PK > 1) {
-                            row_ib = __dp4a(ui4, (int)vpk[b], row_ib);
-                            col_ja = __dp4a((int)(upk[j] & pmask), vfa4, col_ja);
+#pragma unroll
+                            for (int w = 0; w < PW; ++w) {
+                                row_ib = __dp4a(ui[w], (int)vpk[w * npad + b], row_ib);
+                                col_ja = __dp4a((int)(upk[w * npad + j] & pm[w]), vfa[w], col_ja);
+                            }
+                        }
+                        if constexpr (TG) {
+                            srow[j] = row_ib;
+                            scol[j] = col_ja;
                         }
                         int d;
                         if constexpr (ASYM) {
@@ -942,6 +1033,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         lmin = min(lmin, d);
                     }
                 }
+                const int nxt = i + 1 < n ? i + 1 : 0;  // the next update's location
+                if constexpr (TG) prefetch(nxt);
                 const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, beta, draw, bar, gs);
                 const int js = sel.x, dstar = sel.y;
                 if (js == i) continue;
@@ -951,11 +1044,19 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 // current I[i][fb] and I[js][fa], for the two p-diagonal entries that move
                 int tib = 0, tja = 0;
                 if (t == 0) {
-                    tib = T[i * S + fb];
-                    tja = T[js * S + fa];
-                    if constexpr (PK > 1) {
-                        tib = __dp4a(ui4, (int)vpk[fb], tib);
-                        tja = __dp4a((int)(upk[js] & pmask), vfa4, tja);
+                    if constexpr (TG) {
+                        tib = srow[js];  // gathered with the pending terms
+                        tja = scol[js];
+                    } else {
+                        tib = T[i * S + fb];
+                        tja = T[js * S + fa];
+                        if constexpr (PK > 1) {
+#pragma unroll
+                            for (int w = 0; w < PW; ++w) {
+                                tib = __dp4a(ui[w], (int)vpk[w * npad + fb], tib);
+                                tja = __dp4a((int)(upk[w * npad + js] & pm[w]), vfa[w], tja);
+                            }
+                        }
                     }
                 }
                 apply_swap(i, js, fa, fb, tib, tja);
@@ -968,6 +1069,18 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     if (t == 0) note_target(a, bestE, s, reached);
                 }
                 group_sync<WPR>(bar);
+                if constexpr (TG) {
+                    // the swap moved p(i) and p(js); a rewrite changed the table
+                    if (PK == 1 || flushed || js == nxt) {
+                        prefetch(nxt);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < MAXK; ++k) {
+                            const int j = t + G * k;
+                            if (j == i || j == js) pre_row[k] = T[nxt * S + sp[j]];
+                        }
+                    }
+                }
             }
         }
     }
@@ -1052,8 +1165,8 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(
     int32_t *sp = reinterpret_cast<int32_t *>(body + (TSMEM ? (size_t)n * a.stride * 4 : 0));
     int32_t *sh = sp + npad;
     int32_t *sv = sh + npad;
-    uint32_t *upk = reinterpret_cast<uint32_t *>(sv + a.sv_len);  // [npad], PK > 1 only
-    uint32_t *vpk = upk + npad;
+    uint32_t *upk = reinterpret_cast<uint32_t *>(sv + a.sv_len);  // [PK / 4][npad], PK > 1 only
+    uint32_t *vpk = upk + (PK / 4) * npad;
     for (;;) {
         if (t == 0) gs->item = atomicAdd(a.queue, 1);
         group_sync<WPR>(bar);
@@ -1124,7 +1237,7 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
             int32_t *sh = sp + npad;
             int32_t *sv = sh + npad;
             uint32_t *upk = reinterpret_cast<uint32_t *>(sv + sa.sv_len);
-            uint32_t *vpk = upk + npad;
+            uint32_t *vpk = upk + (PK / 4) * npad;
             int32_t *T = TSMEM ? sT : sa.tables + (size_t)r * n * sa.stride;
             run_replica<DT, MAXK, WPR, PK, !TSMEM, ASYM>(sa, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
         }
@@ -1147,7 +1260,8 @@ int batch_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *descs, 
                  int nunits, int *queue, int grid, int threads, size_t smem, cudaStream_t stream);
 
 // Shapes with a compiled kernel: (MAXK, WPR) with 32 * WPR * MAXK in
-// {32, 64, 128, 256}; the global-table variant only for 256.
+// {32, 64, 128, 256}; the global-table variant only for 256; 16 pending
+// terms only with global tables.
 #define PDIT_SWEEP_SHAPES_COMMON(X)                                                              \
     X(1, 1, true, 1) X(2, 1, true, 1) X(1, 2, true, 1) X(4, 1, true, 1) X(2, 2, true, 1)         \
     X(1, 4, true, 1) X(8, 1, true, 1) X(4, 2, true, 1) X(2, 4, true, 1) X(1, 8, true, 1)         \
@@ -1155,7 +1269,8 @@ int batch_launch(int maxk, int wpr, bool tsmem, int pk, const SweepArgs *descs, 
 #define PDIT_SWEEP_SHAPES_DEFERRED(X)                                                            \
     X(1, 1, true, 4) X(2, 1, true, 4) X(1, 2, true, 4) X(4, 1, true, 4) X(2, 2, true, 4)         \
     X(1, 4, true, 4) X(8, 1, true, 4) X(4, 2, true, 4) X(2, 4, true, 4) X(1, 8, true, 4)         \
-    X(8, 1, false, 4) X(4, 2, false, 4) X(2, 4, false, 4) X(1, 8, false, 4)
+    X(8, 1, false, 4) X(4, 2, false, 4) X(2, 4, false, 4) X(1, 8, false, 4)                      \
+    X(8, 1, false, 16) X(4, 2, false, 16) X(2, 4, false, 16) X(1, 8, false, 16)
 
 #define PDIT_INSTANTIATE_SWEEP(DT, ASYM, SHAPES)                                                          \
     template <int MAXK, int WPR, bool TSMEM, int PK>                                                      \

@@ -135,6 +135,7 @@ def named(name: str, seed: int = 0):
     'n100' : dense 0..99
     'n100a': the general-form analogue of 'n100': every entry of D and F
              drawn independently, uniform 0..99, zero diagonals (asymmetric)
+    'n256' : dense 0..99 at N = 256, the largest size (tables in global memory)
     'c256' : two-level flow at the size of the paper's tai256c: N = 256, flow
              1 between every pair of a 92-facility subset and 0 elsewhere, D
              dense symmetric uniform 1..99 (synthetic values)
@@ -151,6 +152,8 @@ def named(name: str, seed: int = 0):
         return asymmetric(100, 0, 99, seed, 101), asymmetric(100, 0, 99, seed, 103)
     if name == "c256":
         return flow_class_instance(256, 92, seed)
+    if name == "n256":
+        return dense_instance(256, seed)
     raise KeyError(name)
 
 

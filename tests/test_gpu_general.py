@@ -74,13 +74,13 @@ def test_sizes(n, diag):
 
 MAPPINGS = [(40, 1, 1), (40, 2, 1), (40, 1, 4), (40, 2, 4), (100, 1, 1), (100, 4, 1), (100, 2, 4),
             (100, 4, 4), (129, 2, 1), (129, 8, 4), (200, 4, 1), (200, 8, 4), (256, 1, 1), (256, 8, 1),
-            (256, 2, 4), (256, 8, 4)]
+            (256, 2, 4), (256, 8, 4), (256, 8, 16), (200, 4, 16)]
 
 
 @pytest.mark.parametrize("n,wpr,pk", MAPPINGS)
 def test_every_thread_mapping(n, wpr, pk):
-    """Immediate rank-2 updates (1) and deferred ones (4 pending terms = two
-    swaps), shared- and global-memory tables."""
+    """Immediate rank-2 updates (1) and deferred ones (4 or 16 pending terms =
+    two or eight swaps), shared- and global-memory tables."""
     D, F = G.asymmetric_instance(n, seed=n + 3)
     beta = schedule(D, F, 5, 0.5)
     g = gpu_run(D, F, beta, 5, 13, 3, tables=True, wpr=wpr, pk=pk)

@@ -128,7 +128,8 @@ def test_sizes_dense(n):
 MAPPINGS = [(30, 1, 1), (30, 1, 4), (40, 1, 1), (40, 2, 1), (40, 1, 4), (40, 2, 4), (100, 1, 1),
             (100, 2, 1), (100, 4, 1), (100, 1, 4), (100, 2, 4), (100, 4, 4), (129, 1, 1), (129, 2, 4),
             (129, 4, 1), (129, 8, 4), (190, 8, 1), (190, 4, 4), (256, 1, 1), (256, 2, 1), (256, 4, 1),
-            (256, 8, 1), (200, 1, 4), (256, 2, 4), (256, 4, 4), (256, 8, 4)]
+            (256, 8, 1), (200, 1, 4), (256, 2, 4), (256, 4, 4), (256, 8, 4), (256, 8, 16), (256, 1, 16),
+            (200, 2, 16), (230, 4, 16)]
 
 
 @pytest.mark.parametrize("n,wpr,pk", MAPPINGS)
