@@ -268,10 +268,12 @@ def run_ragged(args):
             n = sizes[k]
             if n not in tuned:
                 mid = torch.full((4,), float(betas[k][S // 2].item()), dtype=torch.float32, device=dev)
-                tuned[n] = P.pdit_autotune(q, R, mid, 4)
+                wpr, pk = P.pdit_autotune(q, R, mid, 4)
+                tuned[n] = (wpr, pk, P.pdit_launch_shape(q, R)["replicas_per_cta"])
             else:
                 P.pdit_set_warps_per_replica(q, tuned[n][0])
                 P.pdit_set_pending_swaps(q, tuned[n][1])
+                P.pdit_set_replicas_per_cta(q, tuned[n][2])
     tune_s = time.perf_counter() - t0
     items = [dict(qap=q, replicas=R, sweeps=S, beta=betas[k], seed=0, instance_id=k) for k, q in enumerate(qs)]
     stream = torch.cuda.Stream(dev)
@@ -464,7 +466,9 @@ def main():
     ap.add_argument("--mode", default="anneal", choices=["anneal", "cupim"],
                     help="sequential p-dit sweeps (the paper's PIM) or concurrent updates (its CUPIM)")
     ap.add_argument("--pk", type=int, default=0,
-                    help="accepted swaps held before a table rewrite (0: the library's choice)")
+                    help="pending rank-1 terms held before a table rewrite (0: the library's choice)")
+    ap.add_argument("--rpc", type=int, default=0,
+                    help="replicas per CTA at most (0: the library's choice)")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="override the workload's sweep count (smaller cases for profiling)")
     args = ap.parse_args()
@@ -510,6 +514,8 @@ def main():
         P.pdit_set_warps_per_replica(q, args.wpr)
     if args.pk:
         P.pdit_set_pending_swaps(q, args.pk)
+    if args.rpc:
+        P.pdit_set_replicas_per_cta(q, args.rpc)
     shape = P.pdit_launch_shape(q, replicas)
     beta = P.pdit_beta_schedule(kind, sweeps, P.pdit_beta_max(q))
     dev = torch.device("cuda", local)
@@ -619,7 +625,7 @@ def main():
     traffic = None
     try:
         # the stored DRAM counters describe the default workload's kernel only
-        if args.workload == "n100" and args.mode == "anneal" and not args.wpr and not args.pk:
+        if args.workload == "n100" and args.mode == "anneal" and not (args.wpr or args.pk or args.rpc):
             with open(TRAFFIC_FILE) as fh:
                 tr = json.load(fh)
             if tr.get("source_sha") == kernel_source_sha():

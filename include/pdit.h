@@ -99,16 +99,28 @@ int qap_n(const pdit_qap *h);
 int pdit_set_warps_per_replica(pdit_qap *h, int wpr);
 
 /*
- * pdit_autotune -- time every compiled thread mapping (warps per replica)
- * and table-update batching (1 or 4 pending swaps) valid for this instance
- * on a short run of `replicas` chains over the DEVICE schedule beta[sweeps]
- * (CUDA events on the handle's stream), keep the fastest for later calls on
- * this handle and write it to shape[0] (warps per replica) and shape[1]
- * (pending swaps) when shape is not NULL. Synchronous; allocates and frees
+ * pdit_autotune -- time every compiled thread mapping (warps per replica),
+ * table-update batching (1, 4 or 16 pending terms) and, where the tables live
+ * in global memory, replicas per CTA (1..4 besides the built-in choice) valid
+ * for this instance on a short run of `replicas` chains over the DEVICE
+ * schedule beta[sweeps] (CUDA events on the handle's stream), keep the
+ * fastest for later calls on this handle and write it to shape[0] (warps per
+ * replica) and shape[1] (pending terms) when shape is not NULL
+ * (pdit_launch_shape reports the replicas per CTA). Synchronous; allocates and frees
  * small temporary buffers. Results of later calls do not depend on the
  * choice. Errors: PDIT_EINVAL, PDIT_ENOTSUP, PDIT_ECUDA.
  */
 int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int *shape);
+
+/*
+ * pdit_set_replicas_per_cta -- replica groups per CTA of later calls on this
+ * handle: at most g (1 or more), within what shared memory, the compiled
+ * thread bound and the named barriers allow; 0 restores the built-in choice
+ * (as many as fit; with tables in global memory, as many as keep all
+ * resident tables within three quarters of L2). Results do not depend on it.
+ * Errors: PDIT_EINVAL.
+ */
+int pdit_set_replicas_per_cta(pdit_qap *h, int g);
 
 /*
  * pdit_launch_shape -- the sweep-kernel launch a call with `replicas` chains

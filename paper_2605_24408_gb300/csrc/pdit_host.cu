@@ -42,6 +42,7 @@ struct pdit_qap {
     cudaStream_t stream = nullptr;
     int force_wpr = 0;      // warps per replica; 0 = chosen per launch
     int force_pk = 0;       // pending swaps before a table rewrite; 0 = chosen per launch
+    int force_groups = 0;   // replicas per CTA; 0 = chosen per launch
 };
 
 namespace {
@@ -185,7 +186,7 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk, extra_for(pk));
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
     int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
-    if (!p->tsmem && h->l2_bytes > 0 && h->num_sms > 0) {
+    if (!p->tsmem && h->l2_bytes > 0 && h->num_sms > 0 && h->force_groups <= 0) {
         // Tables in global memory: keep the tables of all resident replicas
         // within three quarters of L2 (one CTA per SM).
         const size_t table = (size_t)4 * n * p->stride;
@@ -204,6 +205,7 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     p->maxk = cover / (32 * wpr);
     int g = std::min(fit, pdit::sweep_bound(p->maxk, wpr) / (32 * wpr));
     if (wpr > 1) g = std::min(g, 15);  // named barriers 1..15
+    if (h->force_groups > 0) g = std::min(g, h->force_groups);
     const int per_sm = (replicas + h->num_sms - 1) / h->num_sms;
     g = std::max(1, std::min(g, per_sm));
     p->groups = g;
@@ -243,6 +245,7 @@ int make_class_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
     p->maxk = cover / (32 * wpr);
     int g = std::min(fit, pdit::class_bound(p->maxk, wpr) / (32 * wpr));
     if (wpr > 1) g = std::min(g, 15);  // named barriers 1..15
+    if (h->force_groups > 0) g = std::min(g, h->force_groups);
     const int per_sm = (replicas + h->num_sms - 1) / h->num_sms;
     g = std::max(1, std::min(g, per_sm));
     p->groups = g;
@@ -652,6 +655,12 @@ int pdit_set_class_update(pdit_qap *h, int enable) {
     return PDIT_OK;
 }
 
+int pdit_set_replicas_per_cta(pdit_qap *h, int g) {
+    if (!h || g < 0) return PDIT_EINVAL;
+    h->force_groups = g;
+    return PDIT_OK;
+}
+
 int pdit_set_pending_swaps(pdit_qap *h, int k) {
     if (!h || (k != 0 && k != 1 && k != 4 && k != 16)) return PDIT_EINVAL;
     h->force_pk = k;
@@ -864,7 +873,7 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     if (!h || replicas < 1 || sweeps < 1 || !beta) return PDIT_EINVAL;
     if (!h->stream) PDIT_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     const int cover = cover_for(h->n);
-    const int keep_wpr = h->force_wpr, keep_pk = h->force_pk;
+    const int keep_wpr = h->force_wpr, keep_pk = h->force_pk, keep_g = h->force_groups;
     int32_t *dperm = nullptr;
     int64_t *dcost = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -872,40 +881,48 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     if (e == cudaSuccess) e = cudaMalloc((void **)&dcost, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int best_wpr = 0, best_pk = 0, rc = PDIT_OK;
+    int best_wpr = 0, best_pk = 0, best_g = 0, rc = PDIT_OK;
     float best_ms = 0.0f;
+    const bool cls = h->cls && h->use_cls;
+    // Candidates: every warps-per-replica and pending-term count; replicas
+    // per CTA = the built-in choice, and 1..4 where the tables live in
+    // global memory (where the built-in choice is an L2-capacity estimate).
     for (int wpr = 1; wpr <= cover / 32 && wpr <= 8 && e == cudaSuccess && rc == PDIT_OK; wpr <<= 1)
-        for (int pk = 1; pk <= 16 && e == cudaSuccess && rc == PDIT_OK; pk *= 4) {
-            const bool cls = h->cls && h->use_cls;
-            if (cls && pk != 1) continue;  // the flow-class kernel keeps no table
-            h->force_wpr = wpr;
-            h->force_pk = pk;
-            Plan p;
-            if ((cls ? make_class_plan(h, replicas, wpr, &p) : make_plan(h, replicas, wpr, pk, &p)) != PDIT_OK)
-                continue;
-            pdit_opts o;
-            pdit_opts_init(&o);
-            o.replicas = replicas;
-            o.sweeps = sweeps;
-            o.seed = 0x5EED;
-            o.beta = beta;
-            o.stream = h->stream;
-            o.best_perm = dperm;
-            o.best_cost = dcost;
-            rc = pdit_anneal_ex(h, &o);  // warm-up (and workspace)
-            if (rc) break;
-            e = cudaEventRecord(e0, h->stream);
-            if (e == cudaSuccess) rc = pdit_anneal_ex(h, &o);
-            if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, h->stream);
-            if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e == cudaSuccess && !rc && (best_wpr == 0 || ms < best_ms)) {
-                best_ms = ms;
-                best_wpr = wpr;
-                best_pk = pk;
+        for (int pk = 1; pk <= 16 && e == cudaSuccess && rc == PDIT_OK; pk *= 4)
+            for (int g = 0; g <= 4 && e == cudaSuccess && rc == PDIT_OK; ++g) {
+                if (cls && pk != 1) continue;  // the flow-class kernel keeps no table
+                h->force_wpr = wpr;
+                h->force_pk = pk;
+                h->force_groups = 0;
+                Plan p;
+                if ((cls ? make_class_plan(h, replicas, wpr, &p) : make_plan(h, replicas, wpr, pk, &p)) != PDIT_OK)
+                    continue;
+                if (g > 0 && (cls || p.tsmem || g == p.groups)) continue;
+                h->force_groups = g;
+                pdit_opts o;
+                pdit_opts_init(&o);
+                o.replicas = replicas;
+                o.sweeps = sweeps;
+                o.seed = 0x5EED;
+                o.beta = beta;
+                o.stream = h->stream;
+                o.best_perm = dperm;
+                o.best_cost = dcost;
+                rc = pdit_anneal_ex(h, &o);  // warm-up (and workspace)
+                if (rc) break;
+                e = cudaEventRecord(e0, h->stream);
+                if (e == cudaSuccess) rc = pdit_anneal_ex(h, &o);
+                if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, h->stream);
+                if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && !rc && (best_wpr == 0 || ms < best_ms)) {
+                    best_ms = ms;
+                    best_wpr = wpr;
+                    best_pk = pk;
+                    best_g = g;
+                }
             }
-        }
     cudaFree(dperm);
     cudaFree(dcost);
     if (e0) cudaEventDestroy(e0);
@@ -913,11 +930,13 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     if (rc || e != cudaSuccess || best_wpr == 0) {
         h->force_wpr = keep_wpr;
         h->force_pk = keep_pk;
+        h->force_groups = keep_g;
         if (rc) return rc;
         return e != cudaSuccess ? cuda_fail(e, "pdit_autotune") : PDIT_ENOTSUP;
     }
     h->force_wpr = best_wpr;
     h->force_pk = best_pk;
+    h->force_groups = best_g;
     if (shape) {
         shape[0] = best_wpr;
         shape[1] = best_pk;

@@ -168,6 +168,8 @@ def lib():
     L.pdit_server_result.restype = ctypes.c_int
     L.pdit_server_destroy.argtypes = [vp]
     L.pdit_server_destroy.restype = None
+    L.pdit_set_replicas_per_cta.argtypes = [vp, ctypes.c_int]
+    L.pdit_set_replicas_per_cta.restype = ctypes.c_int
     L.pdit_instance_form.argtypes = [vp]
     L.pdit_instance_form.restype = ctypes.c_int
     L.pdit_set_class_update.argtypes = [vp, ctypes.c_int]
@@ -314,6 +316,10 @@ def pdit_set_class_update(q: Qap, enable: bool):
 
 def pdit_set_warps_per_replica(q: Qap, wpr: int):
     _check(lib().pdit_set_warps_per_replica(q.handle, wpr), "pdit_set_warps_per_replica")
+
+
+def pdit_set_replicas_per_cta(q: Qap, g: int):
+    _check(lib().pdit_set_replicas_per_cta(q.handle, g), "pdit_set_replicas_per_cta")
 
 
 def pdit_set_pending_swaps(q: Qap, k: int):

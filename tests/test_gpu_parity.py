@@ -310,3 +310,39 @@ def test_cupim_matches_oracle(name, n, wpr, pk):
     g = gpu_run(D, F, beta, S, 31, 6, tables=True, wpr=wpr, pk=pk, mode=3)
     r = O.anneal(D, F, beta, S, 31, 0, 6, mode="cupim", threads=6, tables=True)
     check_equal(g, r, tables=True)
+
+
+# --- launch-shape knobs and the autotuner ------------------------------------------
+
+@pytest.mark.parametrize("n,g", [(100, 1), (100, 3), (256, 1), (256, 3)])
+def test_replicas_per_cta_does_not_change_results(n, g):
+    D, F = G.dense_instance(n, seed=n + 9)
+    beta = schedule(D, F, "linear", 6) * np.float32(0.5)
+    p = P()
+    with p.Qap(D, F) as q:
+        p.pdit_set_replicas_per_cta(q, g)
+        assert p.pdit_launch_shape(q, 64)["replicas_per_cta"] <= g
+        dbeta = torch.from_numpy(beta).cuda()
+        out = p.anneal_device(q, 9, dbeta, 6, 4, per_replica=True)
+        torch.cuda.synchronize()
+        g_out = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
+    r = O.anneal(D, F, beta, 6, 4, 0, 9, threads=9)
+    check_equal(g_out, r)
+
+
+@pytest.mark.parametrize("n", [40, 230])
+def test_autotune_keeps_results_and_reports_a_shape(n):
+    D, F = G.dense_instance(n, seed=n + 2)
+    beta = schedule(D, F, "linear", 8)
+    p = P()
+    with p.Qap(D, F) as q:
+        dbeta = torch.from_numpy(beta).cuda()
+        wpr, pk = p.pdit_autotune(q, 32, dbeta, 4)
+        shape = p.pdit_launch_shape(q, 32)
+        assert shape["warps_per_replica"] == wpr and shape["pending_swaps"] == pk
+        assert wpr in (1, 2, 4, 8) and pk in (1, 4, 16)
+        out = p.anneal_device(q, 7, dbeta, 8, 3, per_replica=True)
+        torch.cuda.synchronize()
+        g_out = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
+    r = O.anneal(D, F, beta, 8, 3, 0, 7, threads=7)
+    check_equal(g_out, r)
