@@ -44,11 +44,13 @@ WORKLOADS = {
     "n100a": ("n100a", 4096, 10000, "linear"),
     "c256": ("c256", 4096, 2000, "linear"),
     "n256": ("n256", 2048, 1000, "linear"),
+    "dense": ("dense", 2048, 1000, "linear"),  # N from --dense-n
 }
 WORKLOAD_TEXT = {
     "n100": "dense symmetric QAP N=100 (D, F uniform 0..99)",
     "n100a": "dense asymmetric QAP N=100 (every entry of D and F independent uniform 0..99, zero diagonals)",
     "n256": "dense symmetric QAP N=256 (D, F uniform 0..99): influence tables in global memory",
+    "dense": "dense symmetric QAP (D, F uniform 0..99) of the size given by --dense-n",
     "c256": "two-level flow N=256 (flow 1 between every pair of a 92-facility subset, 0 elsewhere; "
             "D dense symmetric uniform 1..99): the structure of the paper's tai256c, synthetic values",
 }
@@ -269,11 +271,14 @@ def run_ragged(args):
             if n not in tuned:
                 mid = torch.full((4,), float(betas[k][S // 2].item()), dtype=torch.float32, device=dev)
                 wpr, pk = P.pdit_autotune(q, R, mid, 4)
-                tuned[n] = (wpr, pk, P.pdit_launch_shape(q, R)["replicas_per_cta"])
+                shp = P.pdit_launch_shape(q, R)
+                tuned[n] = (wpr, pk, shp["replicas_per_cta"],
+                            P.PDIT_PLACE_SHARED if shp["tables_in_smem"] else P.PDIT_PLACE_GLOBAL)
             else:
                 P.pdit_set_warps_per_replica(q, tuned[n][0])
                 P.pdit_set_pending_swaps(q, tuned[n][1])
                 P.pdit_set_replicas_per_cta(q, tuned[n][2])
+                P.pdit_set_table_placement(q, tuned[n][3])
     tune_s = time.perf_counter() - t0
     items = [dict(qap=q, replicas=R, sweeps=S, beta=betas[k], seed=0, instance_id=k) for k, q in enumerate(qs)]
     stream = torch.cuda.Stream(dev)
@@ -469,6 +474,9 @@ def main():
                     help="pending rank-1 terms held before a table rewrite (0: the library's choice)")
     ap.add_argument("--rpc", type=int, default=0,
                     help="replicas per CTA at most (0: the library's choice)")
+    ap.add_argument("--dense-n", type=int, default=180, help="size of the 'dense' workload")
+    ap.add_argument("--place", type=int, default=0, choices=[0, 1, 2],
+                    help="influence tables: 0 library's choice, 1 shared memory, 2 global memory")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="override the workload's sweep count (smaller cases for profiling)")
     args = ap.parse_args()
@@ -503,7 +511,7 @@ def main():
     inst, replicas, sweeps, kind = WORKLOADS[args.workload]
     if args.sweeps > 0:
         sweeps = args.sweeps
-    D, F = G.named(inst)
+    D, F = G.dense_instance(args.dense_n, 0) if inst == "dense" else G.named(inst)
     n = D.shape[0]
     q = P.Qap(D, F)
     if args.no_class_update:
@@ -516,6 +524,8 @@ def main():
         P.pdit_set_pending_swaps(q, args.pk)
     if args.rpc:
         P.pdit_set_replicas_per_cta(q, args.rpc)
+    if args.place:
+        P.pdit_set_table_placement(q, args.place)
     shape = P.pdit_launch_shape(q, replicas)
     beta = P.pdit_beta_schedule(kind, sweeps, P.pdit_beta_max(q))
     dev = torch.device("cuda", local)
@@ -625,7 +635,7 @@ def main():
     traffic = None
     try:
         # the stored DRAM counters describe the default workload's kernel only
-        if args.workload == "n100" and args.mode == "anneal" and not (args.wpr or args.pk or args.rpc):
+        if args.workload == "n100" and args.mode == "anneal" and not (args.wpr or args.pk or args.rpc or args.place):
             with open(TRAFFIC_FILE) as fh:
                 tr = json.load(fh)
             if tr.get("source_sha") == kernel_source_sha():
@@ -637,7 +647,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "%s: %s" % (args.workload, WORKLOAD_TEXT[args.workload])
+        "config": {"workload": "%s%s: %s" % (args.workload, (" N=%d" % n) if inst == "dense" else "",
+                                             WORKLOAD_TEXT[args.workload])
                    if args.workload in WORKLOAD_TEXT else args.workload,
                    "mode": args.mode,
                    "update": "flow classes" if class_path else "table",

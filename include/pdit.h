@@ -100,9 +100,10 @@ int pdit_set_warps_per_replica(pdit_qap *h, int wpr);
 
 /*
  * pdit_autotune -- time every compiled thread mapping (warps per replica),
- * table-update batching (1, 4 or 16 pending terms) and, where the tables live
- * in global memory, replicas per CTA (1..4 besides the built-in choice) valid
- * for this instance on a short run of `replicas` chains over the DEVICE
+ * table-update batching (1, 4 or 16 pending terms), the table placement
+ * (shared or global memory, when both are possible) and, where the tables
+ * live in global memory, replicas per CTA (1..4 besides the built-in choice)
+ * valid for this instance on a short run of `replicas` chains over the DEVICE
  * schedule beta[sweeps] (CUDA events on the handle's stream), keep the
  * fastest for later calls on this handle and write it to shape[0] (warps per
  * replica) and shape[1] (pending terms) when shape is not NULL
@@ -111,6 +112,19 @@ int pdit_set_warps_per_replica(pdit_qap *h, int wpr);
  * choice. Errors: PDIT_EINVAL, PDIT_ENOTSUP, PDIT_ECUDA.
  */
 int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int *shape);
+
+/* Influence-table placement (pdit_set_table_placement). */
+#define PDIT_PLACE_AUTO 0   /* shared memory when a replica's table fits next to D and F, else global */
+#define PDIT_PLACE_SHARED 1 /* shared memory (PDIT_ENOTSUP at the next call when it does not fit) */
+#define PDIT_PLACE_GLOBAL 2 /* global memory, L2-resident (n > 128 only; PDIT_ENOTSUP otherwise) */
+
+/*
+ * pdit_set_table_placement -- where later calls on this handle keep the
+ * replicas' influence tables. Global tables let more replicas share an SM
+ * at the cost of L2 latency; the autotuner compares the two. Results do not
+ * depend on it. Errors: PDIT_EINVAL.
+ */
+int pdit_set_table_placement(pdit_qap *h, int place);
 
 /*
  * pdit_set_replicas_per_cta -- replica groups per CTA of later calls on this

@@ -43,6 +43,7 @@ struct pdit_qap {
     int force_wpr = 0;      // warps per replica; 0 = chosen per launch
     int force_pk = 0;       // pending swaps before a table rewrite; 0 = chosen per launch
     int force_groups = 0;   // replicas per CTA; 0 = chosen per launch
+    int force_place = 0;    // influence tables: 0 = shared memory when they fit, 1 = shared, 2 = global
 };
 
 namespace {
@@ -156,8 +157,14 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     p->df_bytes = align_up((size_t)2 * n * p->dstride * h->dt_bytes, 16);
     const size_t budget = h->smem_optin - reserve;
     p->tsmem = true;
-    p->tsmem = p->df_bytes + group_bytes_for(n, p->stride, cover, true, 1, extra_for(1)) <= budget;
-    if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;
+    const size_t g_smem = group_bytes_for(n, p->stride, cover, true, 1, extra_for(1));
+    const bool fits = p->df_bytes + g_smem <= budget;
+    if (h->force_place == 1 && !fits) return PDIT_ENOTSUP;
+    p->tsmem = h->force_place == 2 ? false : fits;
+    // Built-in choice: where shared memory holds a single replica per SM,
+    // L2-resident tables (two or more replicas per SM) are faster.
+    if (h->force_place == 0 && fits && cover == 256 && (budget - p->df_bytes) / g_smem < 2) p->tsmem = false;
+    if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;  // global-table kernels: 32 * WPR * MAXK = 256
     const bool defer_ok = h->packed_ok != 0;
     if (pk != 0 && pk != 1 && pk != 4 && pk != 16) return PDIT_EINVAL;
     if (pk > 1 && !defer_ok) return PDIT_ENOTSUP;
@@ -186,12 +193,11 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     p->group_bytes = group_bytes_for(n, p->stride, cover, p->tsmem, pk, extra_for(pk));
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
     int fit = (int)((budget - p->df_bytes) / p->group_bytes);  // replicas per CTA by memory
-    if (!p->tsmem && h->l2_bytes > 0 && h->num_sms > 0 && h->force_groups <= 0) {
-        // Tables in global memory: keep the tables of all resident replicas
-        // within three quarters of L2 (one CTA per SM).
+    int l2_cap = 1 << 30;  // resident replicas per SM whose tables fit three quarters of L2
+    if (!p->tsmem && h->l2_bytes > 0 && h->num_sms > 0) {
         const size_t table = (size_t)4 * n * p->stride;
-        const int cap = (int)std::max<size_t>(1, (h->l2_bytes * 3 / 4) / (table * (size_t)h->num_sms));
-        fit = std::min(fit, cap);
+        l2_cap = (int)std::max<size_t>(1, (h->l2_bytes * 3 / 4) / (table * (size_t)h->num_sms));
+        if (h->force_groups <= 0) fit = std::min(fit, l2_cap);
     }
     if (wpr <= 0) {
         // Aim for about 16 resident warps per SM to hide the latency of each
@@ -215,7 +221,7 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     int e = sweep_blocks(h->dt_bytes, h->asym != 0, *p, &bps);
     if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
     if (bps < 1) bps = 1;
-    if (!p->tsmem) bps = 1;
+    if (!p->tsmem) bps = std::max(1, std::min(bps, l2_cap / g));  // CTAs per SM within the L2 cap
     const int need = (replicas + g - 1) / g;
     p->grid = std::max(1, std::min(need, h->num_sms * bps));
     return PDIT_OK;
@@ -655,6 +661,12 @@ int pdit_set_class_update(pdit_qap *h, int enable) {
     return PDIT_OK;
 }
 
+int pdit_set_table_placement(pdit_qap *h, int place) {
+    if (!h || place < PDIT_PLACE_AUTO || place > PDIT_PLACE_GLOBAL) return PDIT_EINVAL;
+    h->force_place = place;
+    return PDIT_OK;
+}
+
 int pdit_set_replicas_per_cta(pdit_qap *h, int g) {
     if (!h || g < 0) return PDIT_EINVAL;
     h->force_groups = g;
@@ -874,6 +886,7 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     if (!h->stream) PDIT_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     const int cover = cover_for(h->n);
     const int keep_wpr = h->force_wpr, keep_pk = h->force_pk, keep_g = h->force_groups;
+    const int keep_place = h->force_place;
     int32_t *dperm = nullptr;
     int64_t *dcost = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -881,22 +894,35 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     if (e == cudaSuccess) e = cudaMalloc((void **)&dcost, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int best_wpr = 0, best_pk = 0, best_g = 0, rc = PDIT_OK;
+    int best_wpr = 0, best_pk = 0, best_g = 0, best_place = 0, rc = PDIT_OK;
     float best_ms = 0.0f;
     const bool cls = h->cls && h->use_cls;
-    // Candidates: every warps-per-replica and pending-term count; replicas
-    // per CTA = the built-in choice, and 1..4 where the tables live in
-    // global memory (where the built-in choice is an L2-capacity estimate).
+    // Candidates: the table placement (shared memory when it fits, or
+    // global memory), every warps-per-replica and pending-term count, and
+    // replicas per CTA = the built-in choice, plus 1..4 where the tables
+    // live in global memory (where the built-in choice is an L2-capacity
+    // estimate).
+    for (int place = 0; place <= 2; place += 2)
     for (int wpr = 1; wpr <= cover / 32 && wpr <= 8 && e == cudaSuccess && rc == PDIT_OK; wpr <<= 1)
         for (int pk = 1; pk <= 16 && e == cudaSuccess && rc == PDIT_OK; pk *= 4)
             for (int g = 0; g <= 4 && e == cudaSuccess && rc == PDIT_OK; ++g) {
-                if (cls && pk != 1) continue;  // the flow-class kernel keeps no table
+                if (cls && (pk != 1 || place != 0)) continue;  // the flow-class kernel keeps no table
+                h->force_place = keep_place == 0 ? place : keep_place;
+                if (keep_place != 0 && place != 0) continue;
                 h->force_wpr = wpr;
                 h->force_pk = pk;
                 h->force_groups = 0;
                 Plan p;
                 if ((cls ? make_class_plan(h, replicas, wpr, &p) : make_plan(h, replicas, wpr, pk, &p)) != PDIT_OK)
                     continue;
+                if (place == 2 && keep_place == 0) {
+                    // global placement only as an alternative to shared memory
+                    h->force_place = 0;
+                    Plan q0;
+                    const bool auto_global = make_plan(h, replicas, wpr, pk, &q0) == PDIT_OK && !q0.tsmem;
+                    h->force_place = 2;
+                    if (auto_global) continue;
+                }
                 if (g > 0 && (cls || p.tsmem || g == p.groups)) continue;
                 h->force_groups = g;
                 pdit_opts o;
@@ -921,6 +947,7 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
                     best_wpr = wpr;
                     best_pk = pk;
                     best_g = g;
+                    best_place = h->force_place;
                 }
             }
     cudaFree(dperm);
@@ -931,12 +958,14 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
         h->force_wpr = keep_wpr;
         h->force_pk = keep_pk;
         h->force_groups = keep_g;
+        h->force_place = keep_place;
         if (rc) return rc;
         return e != cudaSuccess ? cuda_fail(e, "pdit_autotune") : PDIT_ENOTSUP;
     }
     h->force_wpr = best_wpr;
     h->force_pk = best_pk;
     h->force_groups = best_g;
+    h->force_place = best_place;
     if (shape) {
         shape[0] = best_wpr;
         shape[1] = best_pk;

@@ -26,6 +26,9 @@ PDIT_ECUDA = -4
 PDIT_EDEVICE = -5
 PDIT_ENOTSUP = -6
 PDIT_EIO = -7
+PDIT_PLACE_AUTO = 0
+PDIT_PLACE_SHARED = 1
+PDIT_PLACE_GLOBAL = 2
 PDIT_FORM_SYMMETRIC = 0
 PDIT_FORM_GENERAL = 1
 PDIT_FORM_FLOW_CLASSES = 2
@@ -168,6 +171,8 @@ def lib():
     L.pdit_server_result.restype = ctypes.c_int
     L.pdit_server_destroy.argtypes = [vp]
     L.pdit_server_destroy.restype = None
+    L.pdit_set_table_placement.argtypes = [vp, ctypes.c_int]
+    L.pdit_set_table_placement.restype = ctypes.c_int
     L.pdit_set_replicas_per_cta.argtypes = [vp, ctypes.c_int]
     L.pdit_set_replicas_per_cta.restype = ctypes.c_int
     L.pdit_instance_form.argtypes = [vp]
@@ -316,6 +321,10 @@ def pdit_set_class_update(q: Qap, enable: bool):
 
 def pdit_set_warps_per_replica(q: Qap, wpr: int):
     _check(lib().pdit_set_warps_per_replica(q.handle, wpr), "pdit_set_warps_per_replica")
+
+
+def pdit_set_table_placement(q: Qap, place: int):
+    _check(lib().pdit_set_table_placement(q.handle, place), "pdit_set_table_placement")
 
 
 def pdit_set_replicas_per_cta(q: Qap, g: int):
