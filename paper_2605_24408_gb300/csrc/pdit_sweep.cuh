@@ -92,7 +92,7 @@ struct SweepArgs {
 struct GroupScratch {
     unsigned long long wtot[8];
     int wmin[8];
-    int sel_j, sel_d, sel_f;  // the drawn outcome: location, energy change, its facility
+    int sel_jf, sel_d, sel_pad;  // the drawn outcome: location | facility << 16, energy change
     int item;
     int stop;
     int cnt, aux0, aux1;
@@ -318,15 +318,13 @@ __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, i
     }
     int js, dstar, fb;
     if constexpr (WPR > 1) {
-        if (own) {
-            gs->sel_j = jloc;
-            gs->sel_d = dsel;
-            gs->sel_f = fsel;
-        }
+        // both below 2^16 (n <= 256): one 64-bit store and load
+        if (own) *reinterpret_cast<int2 *>(&gs->sel_jf) = make_int2(jloc | (fsel << 16), dsel);
         group_sync<WPR>(bar);
-        js = gs->sel_j;
-        dstar = gs->sel_d;
-        fb = gs->sel_f;
+        const int2 sel = *reinterpret_cast<const int2 *>(&gs->sel_jf);
+        js = sel.x & 0xFFFF;
+        fb = sel.x >> 16;
+        dstar = sel.y;
     } else {
         const int src = __ffs(__ballot_sync(kFull, own)) - 1;
         js = __shfl_sync(kFull, jloc, src);
@@ -504,7 +502,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     vq[c2] = cq < nq ? v4[cq] : make_int4(0, 0, 0, 0);
                 }
             }
-#pragma unroll 2
+#pragma unroll 4
             for (int m = wg; m < n; m += WPR) {
                 int um[PW];
 #pragma unroll

@@ -253,6 +253,16 @@ class Qap:
         self.close()
 
 
+def qap_create_host_ptrs(n: int, D_ptr: int, F_ptr: int) -> Qap:
+    """qap_create on raw host pointers (pinned buffers): n x n int32 each."""
+    q = Qap.__new__(Qap)
+    h = ctypes.c_void_p()
+    _check(lib().qap_create(n, ctypes.c_void_p(D_ptr), ctypes.c_void_p(F_ptr), ctypes.byref(h)), "qap_create")
+    q.handle = h
+    q.n = n
+    return q
+
+
 def qap_create(D, F) -> Qap:
     return Qap(D, F)
 
