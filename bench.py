@@ -194,6 +194,25 @@ def cpu_baseline(D, F, beta, n: int, sweeps: int) -> dict:
                       % (cores, cores - 1, sweeps, dt)}
 
 
+def parity_sample(D, F, beta, sweeps: int, mode: str, gpu: dict, reps: int = 4) -> dict:
+    """The oracle on replicas 0..reps-1 of the workload (outside every timed
+    region): their best costs, best sweeps and accepted counts must equal the
+    GPU's; also the number of draws that fell within 1e-6 of a boundary of the
+    exact double-precision Eq. 5 CDF (where an ideal sampler might have chosen
+    another outcome)."""
+    import oracle as O
+
+    r = O.anneal(D, F, beta, sweeps, 0, 0, reps, threads=reps, near=True,
+                 mode="cupim" if mode == "cupim" else "anneal")
+    same = (np.array_equal(gpu["replica_best_cost"][:reps], r["best_cost"]) and
+            np.array_equal(gpu["replica_best_sweep"][:reps], r["best_sweep"]) and
+            np.array_equal(gpu["replica_accepted"][:reps], r["accepted"]))
+    draws = reps * sweeps * D.shape[0]
+    return {"replicas": reps, "bit_exact": bool(same), "draws": draws,
+            "near_boundary_draws": int(r["near_boundary"].sum()),
+            "near_boundary_fraction": float(r["near_boundary"].sum()) / draws}
+
+
 def run_reference(args, wl):
     """--impl reference: the CPU oracle on this host, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -535,6 +554,8 @@ def main():
     outs = {"best_perm": torch.empty(n, dtype=torch.int32, device=dev),
             "best_cost": torch.empty(1, dtype=torch.int64, device=dev),
             "replica_accepted": torch.empty(replicas, dtype=torch.int64, device=dev),
+            "replica_best_cost": torch.empty(replicas, dtype=torch.int64, device=dev),
+            "replica_best_sweep": torch.empty(replicas, dtype=torch.int32, device=dev),
             "status": torch.zeros(1, dtype=torch.int32, device=dev)}
     o = P.opts(replicas=replicas, sweeps=sweeps, seed=0, replica_base=base, beta=dbeta.data_ptr(),
                stream=stream.cuda_stream, mode=P.PDIT_MODE_CUPIM if args.mode == "cupim" else P.PDIT_MODE_ANNEAL)
@@ -687,6 +708,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(D, F, beta, n, sweeps)
+        gpu = {k: outs[k].cpu().numpy() for k in ("replica_best_cost", "replica_best_sweep", "replica_accepted")}
+        line["parity_sample"] = parity_sample(D, F, beta, sweeps, args.mode, gpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     q.close()
