@@ -159,13 +159,16 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     p->tsmem = true;
     const size_t g_smem = group_bytes_for(n, p->stride, cover, true, 1, extra_for(1));
     const bool fits = p->df_bytes + g_smem <= budget;
-    if (h->force_place == 1 && !fits) return PDIT_ENOTSUP;
-    p->tsmem = h->force_place == 2 ? false : fits;
-    // Built-in choice: where shared memory holds a single replica per SM,
-    // L2-resident tables (two or more replicas per SM) are faster.
-    if (h->force_place == 0 && fits && cover == 256 && (budget - p->df_bytes) / g_smem < 2) p->tsmem = false;
-    if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;  // global-table kernels: 32 * WPR * MAXK = 256
     const bool defer_ok = h->packed_ok != 0;
+    if (h->force_place == PDIT_PLACE_SHARED && !fits) return PDIT_ENOTSUP;
+    p->tsmem = h->force_place == PDIT_PLACE_GLOBAL ? false : fits;
+    // Built-in choice: where shared memory holds a single replica per SM,
+    // L2-resident tables (two or more replicas per SM, 16 pending terms) are
+    // faster.
+    if (h->force_place == PDIT_PLACE_AUTO && fits && defer_ok && cover == 256 &&
+        (budget - p->df_bytes) / g_smem < 2)
+        p->tsmem = false;
+    if (!p->tsmem && cover < 256) return PDIT_ENOTSUP;  // global-table kernels: 32 * WPR * MAXK = 256
     if (pk != 0 && pk != 1 && pk != 4 && pk != 16) return PDIT_EINVAL;
     if (pk > 1 && !defer_ok) return PDIT_ENOTSUP;
     if (pk == 16 && p->tsmem) return PDIT_ENOTSUP;  // compiled for global tables only
@@ -884,9 +887,46 @@ int pdit_beta_max(const pdit_qap *h, double *beta_max) {
 int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int *shape) {
     if (!h || replicas < 1 || sweeps < 1 || !beta) return PDIT_EINVAL;
     if (!h->stream) PDIT_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    struct Knobs {
+        int place, wpr, pk, groups;
+    };
+    const Knobs keep{h->force_place, h->force_wpr, h->force_pk, h->force_groups};
+    auto set = [h](const Knobs &k) {
+        h->force_place = k.place;
+        h->force_wpr = k.wpr;
+        h->force_pk = k.pk;
+        h->force_groups = k.groups;
+    };
+    const bool cls = h->cls && h->use_cls;
+    auto plan_ok = [&](const Knobs &k, Plan *p) {
+        set(k);
+        return (cls ? make_class_plan(h, replicas, k.wpr, p) : make_plan(h, replicas, k.wpr, k.pk, p)) == PDIT_OK;
+    };
+    // Candidates: the table placement (a caller's choice, else the built-in
+    // one and, where that keeps the tables in shared memory, global memory),
+    // every warps-per-replica and pending-term count, and replicas per CTA =
+    // the built-in choice plus 1..4 where the tables live in global memory
+    // (there the built-in choice is an L2-capacity estimate). The flow-class
+    // kernel keeps no table: only its warps per replica vary.
+    std::vector<Knobs> cand;
     const int cover = cover_for(h->n);
-    const int keep_wpr = h->force_wpr, keep_pk = h->force_pk, keep_g = h->force_groups;
-    const int keep_place = h->force_place;
+    for (int place : {keep.place, (int)PDIT_PLACE_GLOBAL}) {
+        if (place == PDIT_PLACE_GLOBAL && (keep.place != 0 || cls)) continue;
+        for (int wpr = 1; wpr <= cover / 32 && wpr <= 8; wpr <<= 1)
+            for (int pk : {1, 4, 16}) {
+                if (cls && pk != 1) continue;
+                Plan p;
+                if (!plan_ok({place, wpr, pk, 0}, &p)) continue;
+                if (place == PDIT_PLACE_GLOBAL) {
+                    Plan q;
+                    if (plan_ok({0, wpr, pk, 0}, &q) && !q.tsmem) continue;  // already the built-in choice
+                }
+                cand.push_back({place, wpr, pk, 0});
+                if (!cls && !p.tsmem)
+                    for (int g = 1; g <= 4; ++g)
+                        if (g != p.groups) cand.push_back({place, wpr, pk, g});
+            }
+    }
     int32_t *dperm = nullptr;
     int64_t *dcost = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -894,81 +934,45 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     if (e == cudaSuccess) e = cudaMalloc((void **)&dcost, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int best_wpr = 0, best_pk = 0, best_g = 0, best_place = 0, rc = PDIT_OK;
+    int rc = PDIT_OK, best = -1;
     float best_ms = 0.0f;
-    const bool cls = h->cls && h->use_cls;
-    // Candidates: the table placement (shared memory when it fits, or
-    // global memory), every warps-per-replica and pending-term count, and
-    // replicas per CTA = the built-in choice, plus 1..4 where the tables
-    // live in global memory (where the built-in choice is an L2-capacity
-    // estimate).
-    for (int place = 0; place <= 2; place += 2)
-    for (int wpr = 1; wpr <= cover / 32 && wpr <= 8 && e == cudaSuccess && rc == PDIT_OK; wpr <<= 1)
-        for (int pk = 1; pk <= 16 && e == cudaSuccess && rc == PDIT_OK; pk *= 4)
-            for (int g = 0; g <= 4 && e == cudaSuccess && rc == PDIT_OK; ++g) {
-                if (cls && (pk != 1 || place != 0)) continue;  // the flow-class kernel keeps no table
-                h->force_place = keep_place == 0 ? place : keep_place;
-                if (keep_place != 0 && place != 0) continue;
-                h->force_wpr = wpr;
-                h->force_pk = pk;
-                h->force_groups = 0;
-                Plan p;
-                if ((cls ? make_class_plan(h, replicas, wpr, &p) : make_plan(h, replicas, wpr, pk, &p)) != PDIT_OK)
-                    continue;
-                if (place == 2 && keep_place == 0) {
-                    // global placement only as an alternative to shared memory
-                    h->force_place = 0;
-                    Plan q0;
-                    const bool auto_global = make_plan(h, replicas, wpr, pk, &q0) == PDIT_OK && !q0.tsmem;
-                    h->force_place = 2;
-                    if (auto_global) continue;
-                }
-                if (g > 0 && (cls || p.tsmem || g == p.groups)) continue;
-                h->force_groups = g;
-                pdit_opts o;
-                pdit_opts_init(&o);
-                o.replicas = replicas;
-                o.sweeps = sweeps;
-                o.seed = 0x5EED;
-                o.beta = beta;
-                o.stream = h->stream;
-                o.best_perm = dperm;
-                o.best_cost = dcost;
-                rc = pdit_anneal_ex(h, &o);  // warm-up (and workspace)
-                if (rc) break;
-                e = cudaEventRecord(e0, h->stream);
-                if (e == cudaSuccess) rc = pdit_anneal_ex(h, &o);
-                if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, h->stream);
-                if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (e == cudaSuccess && !rc && (best_wpr == 0 || ms < best_ms)) {
-                    best_ms = ms;
-                    best_wpr = wpr;
-                    best_pk = pk;
-                    best_g = g;
-                    best_place = h->force_place;
-                }
-            }
+    for (size_t c = 0; c < cand.size() && e == cudaSuccess && rc == PDIT_OK; ++c) {
+        set(cand[c]);
+        pdit_opts o;
+        pdit_opts_init(&o);
+        o.replicas = replicas;
+        o.sweeps = sweeps;
+        o.seed = 0x5EED;
+        o.beta = beta;
+        o.stream = h->stream;
+        o.best_perm = dperm;
+        o.best_cost = dcost;
+        rc = pdit_anneal_ex(h, &o);  // warm-up (and workspace)
+        if (rc) break;
+        e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess) rc = pdit_anneal_ex(h, &o);
+        if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && !rc && (best < 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = (int)c;
+        }
+    }
     cudaFree(dperm);
     cudaFree(dcost);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (rc || e != cudaSuccess || best_wpr == 0) {
-        h->force_wpr = keep_wpr;
-        h->force_pk = keep_pk;
-        h->force_groups = keep_g;
-        h->force_place = keep_place;
+    if (rc || e != cudaSuccess || best < 0) {
+        set(keep);
         if (rc) return rc;
         return e != cudaSuccess ? cuda_fail(e, "pdit_autotune") : PDIT_ENOTSUP;
     }
-    h->force_wpr = best_wpr;
-    h->force_pk = best_pk;
-    h->force_groups = best_g;
-    h->force_place = best_place;
+    set(cand[best]);
     if (shape) {
-        shape[0] = best_wpr;
-        shape[1] = best_pk;
+        shape[0] = cand[best].wpr;
+        shape[1] = cand[best].pk;
     }
     return PDIT_OK;
 }

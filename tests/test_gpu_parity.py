@@ -353,3 +353,20 @@ def test_autotune_keeps_results_and_reports_a_shape(n):
         g_out = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
     r = O.anneal(D, F, beta, 8, 3, 0, 7, threads=7)
     check_equal(g_out, r)
+
+
+def test_wide_values_at_a_single_replica_size_stay_in_shared_memory():
+    """N = 150 with D up to 300 (int16 staging; swap factors do not fit a
+    byte, so no pending terms): one table fits shared memory next to D and F,
+    and without pending terms the tables stay there."""
+    n = 150
+    D = G.random_symmetric(n, 0, 300, seed=5, tag=1)
+    F = G.random_symmetric(n, 0, 50, seed=6, tag=2)
+    p = P()
+    with p.Qap(D, F) as q:
+        shape = p.pdit_launch_shape(q, 64)
+        assert shape["tables_in_smem"] == 1 and shape["pending_swaps"] == 1
+    beta = schedule(D, F, "linear", 6)
+    g = gpu_run(D, F, beta, 6, 2, 4, tables=True)
+    r = O.anneal(D, F, beta, 6, 2, 0, 4, threads=4, tables=True)
+    check_equal(g, r, tables=True)
