@@ -58,8 +58,10 @@ METRIC = "p-dit updates/s"
 L2_FLUSH_BYTES = 512 << 20
 SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM per clock (32 banks x 4 B)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_kernel_n100_traffic.json")
+# the sweep kernel's own sources; the stored DRAM counters also record the
+# launch shape they were taken with, and both must match to be reported
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_24408_gb300", "csrc", f)
-                  for f in ("pdit_sweep.cuh", "pdit_host.cu")]
+                  for f in ("pdit_sweep.cuh", "pdit_sweep_i8.cu")]
 
 
 def kernel_source_sha() -> str:
@@ -670,7 +672,7 @@ def main():
         if args.workload == "n100" and args.mode == "anneal" and not (args.wpr or args.pk or args.rpc or args.place):
             with open(TRAFFIC_FILE) as fh:
                 tr = json.load(fh)
-            if tr.get("source_sha") == kernel_source_sha():
+            if tr.get("source_sha") == kernel_source_sha() and tr.get("launch") == shape:
                 traffic = tr.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
