@@ -109,6 +109,7 @@ __device__ __forceinline__ void run_class_replica(const SweepArgs &a, int r, int
                 const DT *Di = sD + i * n;
                 // ---- swap energies: 0 within a class, 2 f (G_w - G_u - D_uw) across
                 int lmin = 0x7FFFFFFF;
+                int dself = 0;  // MAXK = 1: this thread's energy, handed to the draw in a register
 #pragma unroll
                 for (int k = 0; k < MAXK; ++k) {
                     const int j = t + G * k;
@@ -118,11 +119,14 @@ __device__ __forceinline__ void run_class_replica(const SweepArgs &a, int r, int
                             const int gd = sG[j] - gi;
                             d = f2 * ((xa ? gd : -gd) - (int)Di[j]);
                         }
-                        sv[j] = d;
+                        if constexpr (MAXK > 1)
+                            sv[j] = d;
+                        else
+                            dself = d;
                         lmin = min(lmin, d);
                     }
                 }
-                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, beta, draw, bar, gs);
+                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, dself, beta, draw, bar, gs);
                 const int js = sel.x, dstar = sel.y, fb = sel.z;
                 if (js == i) continue;
                 const int fa = sp[i];

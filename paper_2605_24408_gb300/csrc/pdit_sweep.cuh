@@ -243,7 +243,9 @@ __device__ __forceinline__ void fisher_yates(const SweepArgs &a, uint32_t grep, 
 
 // ---------------------------------------------------------------------------
 // Eq. 5 draw over the n outcomes whose swap energies the group has written to
-// sv[0..n) (lmin: the minimum over this thread's own candidates): group
+// sv[0..n) (with one candidate per thread, MAXK = 1, each thread passes its
+// own energy in dself instead and sv is not read; lmin: the minimum over this
+// thread's own candidates): group
 // minimum, binary32 weights of the shifted energies, thread-contiguous 64-bit
 // prefix sums (thread t holds outcomes t*MAXK .. t*MAXK + MAXK - 1), the
 // 64-bit draw scaled by the total, and the first outcome whose inclusive
@@ -255,7 +257,8 @@ __device__ __forceinline__ void fisher_yates(const SweepArgs &a, uint32_t grep, 
 // ---------------------------------------------------------------------------
 template <int MAXK, int WPR>
 __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, int n, int t, int lmin,
-                                         float beta, unsigned long long draw, int bar, GroupScratch *gs) {
+                                         int dself, float beta, unsigned long long draw, int bar,
+                                         GroupScratch *gs) {
     const int lane = t & 31;
     const int wg = t >> 5;
     int dmin = __reduce_min_sync(kFull, lmin);
@@ -271,7 +274,10 @@ __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, i
 
     // ---- sample: thread-contiguous weights, 64-bit prefix sums
     int dc[MAXK];
-    load_block<MAXK>(sv, t, dc);
+    if constexpr (MAXK == 1)
+        dc[0] = dself;
+    else
+        load_block<MAXK>(sv, t, dc);
     unsigned long long pre[MAXK];
     unsigned long long lsum = 0;
 #pragma unroll
@@ -982,6 +988,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
 
                 // ---- gather: Eq. 3 for every candidate j
                 int lmin = 0x7FFFFFFF;
+                int dself = 0;  // MAXK = 1: this thread's energy, handed to the draw in a register
 #pragma unroll
                 for (int k = 0; k < MAXK; ++k) {
                     const int j = t + G * k;
@@ -1027,13 +1034,16 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                                      ((int)Fa[fa] + (int)sF[b * n + b] - 2 * fab);
                         }
                         if (j == i) d = 0;
-                        sv[j] = d;
+                        if constexpr (MAXK > 1)
+                            sv[j] = d;
+                        else
+                            dself = d;
                         lmin = min(lmin, d);
                     }
                 }
                 const int nxt = i + 1 < n ? i + 1 : 0;  // the next update's location
                 if constexpr (TG) prefetch(nxt);
-                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, beta, draw, bar, gs);
+                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, dself, beta, draw, bar, gs);
                 const int js = sel.x, dstar = sel.y;
                 if (js == i) continue;
 
