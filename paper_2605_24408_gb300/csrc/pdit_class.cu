@@ -126,7 +126,7 @@ __device__ __forceinline__ void run_class_replica(const SweepArgs &a, int r, int
                         lmin = min(lmin, d);
                     }
                 }
-                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, dself, beta, draw, bar, gs);
+                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, dself, MAXK == 1 && t < n ? sp[t] : 0, beta, draw, bar, gs);
                 const int js = sel.x, dstar = sel.y, fb = sel.z;
                 if (js == i) continue;
                 const int fa = sp[i];

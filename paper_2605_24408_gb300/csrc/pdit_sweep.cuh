@@ -244,8 +244,8 @@ __device__ __forceinline__ void fisher_yates(const SweepArgs &a, uint32_t grep, 
 // ---------------------------------------------------------------------------
 // Eq. 5 draw over the n outcomes whose swap energies the group has written to
 // sv[0..n) (with one candidate per thread, MAXK = 1, each thread passes its
-// own energy in dself instead and sv is not read; lmin: the minimum over this
-// thread's own candidates): group
+// own energy in dself and its location's facility in pself instead, and sv is
+// not read; lmin: the minimum over this thread's own candidates): group
 // minimum, binary32 weights of the shifted energies, thread-contiguous 64-bit
 // prefix sums (thread t holds outcomes t*MAXK .. t*MAXK + MAXK - 1), the
 // 64-bit draw scaled by the total, and the first outcome whose inclusive
@@ -257,8 +257,8 @@ __device__ __forceinline__ void fisher_yates(const SweepArgs &a, uint32_t grep, 
 // ---------------------------------------------------------------------------
 template <int MAXK, int WPR>
 __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, int n, int t, int lmin,
-                                         int dself, float beta, unsigned long long draw, int bar,
-                                         GroupScratch *gs) {
+                                         int dself, int pself, float beta, unsigned long long draw,
+                                         int bar, GroupScratch *gs) {
     const int lane = t & 31;
     const int wg = t >> 5;
     int dmin = __reduce_min_sync(kFull, lmin);
@@ -320,7 +320,10 @@ __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, i
         for (int k = 0; k < MAXK; ++k)
             if (k == kk) dsel = dc[k];
         jloc = t * MAXK + kk;
-        fsel = sp[jloc];
+        if constexpr (MAXK == 1)
+            fsel = pself;
+        else
+            fsel = sp[jloc];
     }
     int js, dstar, fb;
     if constexpr (WPR > 1) {
@@ -741,6 +744,28 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             }
         }
     };
+    // One candidate per thread (MAXK = 1): thread t owns location t and keeps
+    // p(t), h(t) and its packed u factors in registers for the gathers;
+    // shared memory stays the copy that is written (and that other threads
+    // read), and the owner refreshes its registers after every swap.
+    constexpr bool OWN = MAXK == 1;
+    int myp = 0, myh = 0;
+    uint32_t myu[PW];
+#pragma unroll
+    for (int w = 0; w < PW; ++w) myu[w] = 0u;
+    auto refresh_own = [&]() {
+        if constexpr (OWN) {
+            if (t < n) {
+                myp = sp[t];
+                myh = sh[t];
+                if constexpr (PK > 1) {
+#pragma unroll
+                    for (int w = 0; w < PW; ++w) myu[w] = upk[w * npad + t];
+                }
+            }
+        }
+    };
+    refresh_own();
     int32_t *srow = sv + a.rc_off;  // TG: gathered row values T[i][p(j)] by j, then the column values
     int32_t *scol = srow + npad;
     if constexpr (TG) {
@@ -993,7 +1018,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 for (int k = 0; k < MAXK; ++k) {
                     const int j = t + G * k;
                     if (j < n) {
-                        const int b = sp[j];
+                        const int b = OWN ? myp : sp[j];
+                        const int hj = OWN ? myh : sh[j];
                         const int dij = Di[j];
                         const int fab = Fa[b];
                         int row_ib, col_ja;
@@ -1007,8 +1033,9 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         if constexpr (PK > 1) {
 #pragma unroll
                             for (int w = 0; w < PW; ++w) {
+                                const uint32_t uj = OWN ? myu[w] : upk[w * npad + j];
                                 row_ib = __dp4a(ui[w], (int)vpk[w * npad + b], row_ib);
-                                col_ja = __dp4a((int)(upk[w * npad + j] & pm[w]), vfa[w], col_ja);
+                                col_ja = __dp4a((int)(uj & pm[w]), vfa[w], col_ja);
                             }
                         }
                         if constexpr (TG) {
@@ -1019,14 +1046,14 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                         if constexpr (ASYM) {
                             const int dji = sD[j * dn + i];
                             const int fba = sF[b * dn + fa];
-                            d = row_ib - hi + col_ja - sh[j];
+                            d = row_ib - hi + col_ja - hj;
                             if (zero_diag)
                                 d += (dij + dji) * (fab + fba);
                             else
                                 d += ((int)Di[i] + (int)sD[j * dn + j] - dij - dji) *
                                      ((int)Fa[fa] + (int)sF[b * dn + b] - fab - fba);
                         } else {
-                            d = 2 * (row_ib - hi + col_ja - sh[j]);
+                            d = 2 * (row_ib - hi + col_ja - hj);
                             if (zero_diag)
                                 d += 4 * dij * fab;
                             else
@@ -1043,7 +1070,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                 }
                 const int nxt = i + 1 < n ? i + 1 : 0;  // the next update's location
                 if constexpr (TG) prefetch(nxt);
-                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, dself, beta, draw, bar, gs);
+                const int3 sel = eq5_draw<MAXK, WPR>(sv, sp, n, t, lmin, dself, myp, beta, draw, bar, gs);
                 const int js = sel.x, dstar = sel.y;
                 if (js == i) continue;
 
@@ -1077,6 +1104,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
                     if (t == 0) note_target(a, bestE, s, reached);
                 }
                 group_sync<WPR>(bar);
+                refresh_own();
                 if constexpr (TG) {
                     // the swap moved p(i) and p(js); a rewrite changed the table
                     if (PK == 1 || flushed || js == nxt) {
