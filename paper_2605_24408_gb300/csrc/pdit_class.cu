@@ -87,6 +87,18 @@ __device__ __forceinline__ void run_class_replica(const SweepArgs &a, int r, int
     const float beta_fixed = a.sweep_end <= a.sweep_begin ? 0.0f
                            : a.mode == 1 ? a.beta[a.rung[r]] : a.mode == 2 ? a.beta[r] : 0.0f;
 
+    // Each thread keeps, for its candidates j = t + G k, the class bit of the
+    // facility at j and G_j in registers; it also applies the G update for
+    // exactly these j, so they stay equal to shared memory, which keeps the
+    // copies other threads read (G_i at the start of every update).
+    int cx[MAXK], cg[MAXK];
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k) {
+        const int j = t + G * k;
+        cx[k] = j < n ? sx[sp[j]] : 0;
+        cg[k] = j < n ? sG[j] : 0;
+    }
+
     for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
         if (a.stop) {
             if (t == 0) gs->stop = *reinterpret_cast<volatile int *>(a.done);
@@ -115,8 +127,8 @@ __device__ __forceinline__ void run_class_replica(const SweepArgs &a, int r, int
                     const int j = t + G * k;
                     if (j < n) {
                         int d = 0;
-                        if (sx[sp[j]] != xa) {
-                            const int gd = sG[j] - gi;
+                        if (cx[k] != xa) {
+                            const int gd = cg[k] - gi;
                             d = f2 * ((xa ? gd : -gd) - (int)Di[j]);
                         }
                         if constexpr (MAXK > 1)
@@ -130,13 +142,27 @@ __device__ __forceinline__ void run_class_replica(const SweepArgs &a, int r, int
                 const int js = sel.x, dstar = sel.y, fb = sel.z;
                 if (js == i) continue;
                 const int fa = sp[i];
+                const int xb = sx[fb];
                 // ---- apply: G moves only when the classes differ
-                if (sx[fb] != xa) {
+                if (xb != xa) {
                     const DT *Dj = sD + js * n;
-                    for (int m = t; m < n; m += G) {
-                        const int dd = (int)Dj[m] - (int)Di[m];
-                        sG[m] += xa ? dd : -dd;
+#pragma unroll
+                    for (int k = 0; k < MAXK; ++k) {
+                        const int m = t + G * k;
+                        if (m < n) {
+                            const int dd = (int)Dj[m] - (int)Di[m];
+                            const int v = xa ? dd : -dd;
+                            sG[m] += v;
+                            cg[k] += v;
+                        }
                     }
+                }
+                // the facilities at i and js moved
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k) {
+                    const int j = t + G * k;
+                    if (j == i) cx[k] = xb;
+                    if (j == js) cx[k] = xa;
                 }
                 E += dstar;
                 acc_moves += 1;
