@@ -632,8 +632,23 @@ def main():
                 setter(qe, v)
         if args.no_class_update:
             P.pdit_set_class_update(qe, False)
-        rc = P.pdit_anneal_host_ptrs(qe, replicas, hbeta.data_ptr(), sweeps, 0, hperm.data_ptr(),
-                                     hcost.data_ptr())
+        if args.mode == "anneal":
+            rc = P.pdit_anneal_host_ptrs(qe, replicas, hbeta.data_ptr(), sweeps, 0, hperm.data_ptr(),
+                                         hcost.data_ptr())
+        else:
+            # pdit_anneal runs the sequential sweep; other modes go through
+            # pdit_anneal_ex with the host copies inside the timed region
+            ebeta = hbeta.to(dev, non_blocking=True)
+            eperm = torch.empty(n, dtype=torch.int32, device=dev)
+            ecost = torch.empty(1, dtype=torch.int64, device=dev)
+            eo = P.opts(replicas=replicas, sweeps=sweeps, seed=0, beta=ebeta.data_ptr(),
+                        stream=stream.cuda_stream, mode=P.PDIT_MODE_CUPIM,
+                        best_perm=eperm.data_ptr(), best_cost=ecost.data_ptr())
+            P.pdit_anneal_ex(qe, eo)
+            rc = 0
+            hperm.copy_(eperm, non_blocking=True)
+            hcost.copy_(ecost, non_blocking=True)
+            torch.cuda.synchronize()
         qe.close()
         t1 = time.perf_counter()
         if rc != 0:
