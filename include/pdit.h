@@ -47,7 +47,7 @@ extern "C" {
 #define PDIT_ENOMEM (-3)  /* an allocation failed, or the caller's workspace is too small */
 #define PDIT_ECUDA (-4)   /* a CUDA runtime call failed; see pdit_last_error() */
 #define PDIT_EDEVICE (-5) /* a device-side consistency audit failed (see PDIT_STATUS_*) */
-#define PDIT_ENOTSUP (-6) /* a valid request this build cannot run */
+#define PDIT_ENOTSUP (-6) /* a valid request the compiled kernels cannot run */
 #define PDIT_EIO (-7)     /* a file could not be opened, read or written */
 
 /* Largest instance size. */

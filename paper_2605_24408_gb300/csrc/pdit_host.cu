@@ -524,7 +524,7 @@ const char *pdit_strerror(int code) {
     case PDIT_ENOMEM: return "out of memory or workspace too small";
     case PDIT_ECUDA: return "CUDA runtime error";
     case PDIT_EDEVICE: return "device consistency audit failed";
-    case PDIT_ENOTSUP: return "not supported by this build";
+    case PDIT_ENOTSUP: return "not supported by the compiled kernels";
     case PDIT_EIO: return "file could not be opened, read or written";
     default: return "unknown error";
     }
