@@ -433,7 +433,9 @@ int pdit_server_create(size_t device_budget_bytes, int slice_sweeps, int max_act
  * pdit_server_submit -- queue one request: host D, F (n x n int32,
  * symmetric or not, copied), replicas, sweeps, seed, request_id (Philox counter
  * word 0), and beta (host [sweeps]; NULL = the linear schedule
- * 0 -> pdit_beta_max). Thread-safe. *ticket identifies the request.
+ * 0 -> pdit_beta_max). Thread-safe. *ticket identifies the request. The
+ * values of D and F are checked when the request is admitted (as by
+ * qap_create); a request they would make fail ends in state 3.
  * Errors: PDIT_EINVAL, PDIT_ENOMEM.
  */
 int pdit_server_submit(pdit_server *s, int n, const int32_t *D, const int32_t *F, int replicas, int sweeps,

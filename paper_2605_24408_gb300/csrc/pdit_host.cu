@@ -1745,11 +1745,9 @@ void pdit_server_destroy(pdit_server *s) {
 
 int pdit_server_submit(pdit_server *s, int n, const int32_t *D, const int32_t *F, int replicas, int sweeps,
                        uint64_t seed, uint32_t request_id, const float *beta, int64_t *ticket) {
+    // D and F are validated by qap_create when the request is admitted (a
+    // rejected instance ends in the failed state)
     if (!s || !ticket || n < 2 || n > PDIT_N_MAX || !D || !F || replicas < 1 || sweeps < 0) return PDIT_EINVAL;
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-            if (D[(size_t)i * n + j] != D[(size_t)j * n + i] || F[(size_t)i * n + j] != F[(size_t)j * n + i])
-                return PDIT_EINVAL;
     ServerRequest *r = new (std::nothrow) ServerRequest();
     if (!r) return PDIT_ENOMEM;
     r->request_id = request_id;

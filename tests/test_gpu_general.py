@@ -192,3 +192,26 @@ def test_qaplib_file_end_to_end(tmp_path):
     p.write_qaplib_solution(str(sln), perm, cost)
     c2, p2 = p.read_qaplib_solution(str(sln))
     assert c2 == cost and np.array_equal(p2, perm) and O.cost(A, B, p2) == cost
+
+
+def test_resume_is_bit_identical_to_one_run():
+    D, F = G.asymmetric_instance(60, seed=12, diag=True)
+    beta = schedule(D, F, 40)
+    r = O.anneal(D, F, beta, 40, 6, 0, 10, threads=5, tables=True)
+    p = P()
+    with p.Qap(D, F) as q:
+        dbeta = torch.from_numpy(beta).cuda()
+        first = p.anneal_device(q, 10, dbeta, 40, 6, sweep_end=17, per_replica=True)
+        second = p.anneal_device(q, 10, dbeta, 40, 6, sweep_begin=17, resume=True, workspace=first["workspace"],
+                                 per_replica=True, tables=True)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in second.items() if k != "workspace"}
+    check_equal(g, r, tables=True)
+
+
+def test_concurrent_updates_with_global_tables():
+    D, F = G.asymmetric_instance(256, seed=14)
+    beta = schedule(D, F, 4)
+    g = gpu_run(D, F, beta, 4, 8, 3, tables=True, mode=3)
+    r = O.anneal(D, F, beta, 4, 8, 0, 3, mode="cupim", threads=3, tables=True)
+    check_equal(g, r, tables=True)

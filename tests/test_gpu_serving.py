@@ -71,3 +71,45 @@ def test_results_equal_alone_and_in_the_mix(P, budget, slice_sweeps):
         assert cost == acost
         assert np.array_equal(perm, aperm)
     srv.close()
+
+
+def test_forms_mixed_in_one_server(P):
+    """Symmetric, general-form and two-level-flow requests served together
+    (the batched kernels keep a table for every form) give the results of
+    their single-instance calls (the flow-class kernel for the third)."""
+    insts = {5: G.request_instance(5), 900: G.asymmetric_instance(45, seed=900, diag=True),
+             901: G.flow_class_instance(70, 25, seed=901), 902: G.asymmetric_instance(210, seed=902)}
+    replicas, sweeps, seed = 24, 90, 4
+    srv = P.Server(device_budget_bytes=8 << 30, slice_sweeps=30, max_active=8)
+    tickets = {rid: srv.submit(D, F, replicas, sweeps, seed, rid) for rid, (D, F) in insts.items()}
+    while True:
+        a, q = srv.tick()
+        if a == 0 and q == 0:
+            break
+    for rid, (D, F) in insts.items():
+        st, perm, cost, _ = srv.result(tickets[rid])
+        assert st == 2
+        with P.Qap(D, F) as q:
+            beta = P.pdit_beta_schedule("linear", sweeps, P.pdit_beta_max(q))
+            out = P.anneal_device(q, replicas, torch.from_numpy(beta).cuda(), sweeps, seed, instance_id=rid)
+            torch.cuda.synchronize()
+            assert cost == int(out["best_cost"].item())
+            assert np.array_equal(perm, out["best_perm"].cpu().numpy())
+    srv.close()
+
+
+def test_request_out_of_range_fails_at_admission_and_others_complete(P):
+    srv = P.Server(device_budget_bytes=8 << 30, slice_sweeps=20, max_active=4)
+    big = np.full((12, 12), 4000, np.int32)
+    np.fill_diagonal(big, 0)  # 16 (n+2) maxD maxF >= 2^31: rejected by the range rule
+    bad = srv.submit(big, big, 8, 40, 1, 77)
+    D, F = G.request_instance(78)
+    good = srv.submit(D, F, 8, 40, 1, 78)
+    while True:
+        a, q = srv.tick()
+        if a == 0 and q == 0:
+            break
+    assert srv.result(bad)[0] == 3
+    st, perm, cost, _ = srv.result(good)
+    assert st == 2 and sorted(perm) == list(range(D.shape[0]))
+    srv.close()
