@@ -454,3 +454,29 @@ def test_cupim_single_mover_equals_sequential_update():
     assert (r["accepted"] <= 20).all()
     # every permutation of two locations has the same cost
     assert (r["final_cost"] == 30).all()
+
+
+def test_near_boundary_flag_on_constructed_draws():
+    """The near-boundary count flags a draw exactly when its uniform value
+    u = r / 2^64 lies within 1e-6 of a boundary of the exact double-precision
+    Eq. 5 CDF: draws placed on a boundary are flagged, draws midway between
+    two boundaries more than 2e-6 apart are not."""
+    D, F = G.named("n12")
+    n = 12
+    p = O.init_perm(n, 8, 0, 0)
+    beta = np.float32(0.05)
+    flagged = unflagged = 0
+    for i in range(0, n, 2):
+        _, dE, _, _ = O.choose(D, F, p, i, beta, 0)
+        z = np.exp(-np.float64(beta) * (dE - dE.min()).astype(np.float64))
+        c = np.cumsum(z / z.sum())[:-1]  # the n - 1 inner boundaries
+        for k in range(len(c)):
+            r = int(c[k] * 2.0 ** 64) & 0xFFFFFFFFFFFFFFFF
+            assert O.choose(D, F, p, i, beta, r)[3] == 1
+            flagged += 1
+            lo = c[k - 1] if k > 0 else 0.0
+            if c[k] - lo > 2e-6:
+                r = int(0.5 * (lo + c[k]) * 2.0 ** 64)
+                assert O.choose(D, F, p, i, beta, r)[3] == 0
+                unflagged += 1
+    assert flagged > 20 and unflagged > 20
