@@ -13,10 +13,16 @@
 //   sample   group min of dE, binary32 weights (the arithmetic the CPU oracle
 //            states), thread-contiguous 64-bit prefix sums, one 64-bit Philox
 //            draw scaled by the total, first prefix above it
-//   apply    if a swap j* was drawn: I[m][c] += (D[i][m]-D[j*][m]) (F[b][c]-F[a][c])
-//            as int4 read-modify-writes on each thread's rows, then p, the
-//            p-diagonal h and E
+//   apply    if a swap j* was drawn: I[m][c] += (D[i][m]-D[j*][m]) (F[b][c]-F[a][c]),
+//            either at once (int4 read-modify-writes on each thread's rows)
+//            or deferred: the swap's factors are packed as bytes, every
+//            query adds the pending terms with dp4a, and the table is
+//            rewritten once 4 (16 for tables in global memory) terms are
+//            pending; then p, the p-diagonal h and E
 //   best     first occurrence of a new minimum of E (strict <)
+// With one candidate per thread, thread t owns location t and keeps p(t),
+// h(t) and its packed factors in registers. With tables in global memory the
+// next update's row and column gathers are prefetched into registers.
 // Sweeps visit locations 0..N-1 in order. Every integer is exact; the only
 // floating point is the weight computation, made of single correctly rounded
 // IEEE operations so the CPU oracle reproduces it bit for bit.
