@@ -370,3 +370,20 @@ def test_wide_values_at_a_single_replica_size_stay_in_shared_memory():
     g = gpu_run(D, F, beta, 6, 2, 4, tables=True)
     r = O.anneal(D, F, beta, 6, 2, 0, 4, threads=4, tables=True)
     check_equal(g, r, tables=True)
+
+
+def test_very_many_replicas_sampled():
+    """200,000 replicas in one call (the work queue and every per-replica
+    offset at scale): sampled replicas, the last one included, equal the
+    oracle's runs of the same global replica ids."""
+    D, F = G.named("n12")
+    R, sweeps = 200_000, 3
+    beta = schedule(D, F, "linear", sweeps)
+    g = gpu_run(D, F, beta, sweeps, 21, R)
+    for r0 in (0, 65_535, 123_457, R - 3):
+        r = O.anneal(D, F, beta, sweeps, 21, r0, r0 + 3, threads=3)
+        sl = slice(r0, r0 + 3)
+        assert np.array_equal(g["replica_final_perm"][sl], r["final_perm"])
+        assert np.array_equal(g["replica_best_cost"][sl], r["best_cost"])
+        assert np.array_equal(g["replica_accepted"][sl], r["accepted"])
+    assert int(g["best_cost"][0]) == int(g["replica_best_cost"].min())
