@@ -137,6 +137,9 @@ size_t group_bytes_for(int n, int stride, int cover, bool tsmem, int pk, int ext
     return align_up(pdit::kScratchBytes + table + vec + ring, 16);
 }
 
+// Replicas a plan keeps resident at once.
+int resident(const Plan &p, int replicas) { return std::min(replicas, p.grid * p.groups); }
+
 // Launch shape for `replicas` chains of an n-location instance. `wpr` = warps
 // per replica (0: choose).
 int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t reserve = 0,
@@ -173,18 +176,25 @@ int make_plan(const pdit_qap *h, int replicas, int wpr, int pk, Plan *p, size_t 
     if (pk > 1 && !defer_ok) return PDIT_ENOTSUP;
     if (pk == 16 && p->tsmem) return PDIT_ENOTSUP;  // compiled for global tables only
     if (pk == 0) {
-        // Defer table rewrites when the packed factors cost no replica slot
-        // (tables in shared memory: 4 pending terms), and always for tables
-        // in global memory (16 pending terms: each rewrite streams the whole
-        // table through L2).
-        pk = 1;
-        if (defer_ok) {
-            const size_t g1 = group_bytes_for(n, p->stride, cover, p->tsmem, 1, extra_for(1));
-            const size_t g4 = group_bytes_for(n, p->stride, cover, p->tsmem, 4, extra_for(4));
-            if (!p->tsmem)
-                pk = 16;
-            else if ((budget - p->df_bytes) / g4 >= (budget - p->df_bytes) / g1)
-                pk = 4;
+        // Defer table rewrites always for tables in global memory (16
+        // pending terms: each rewrite streams the whole table through L2),
+        // and for tables in shared memory (4 pending terms) unless the packed
+        // factors would leave fewer replicas resident for this call.
+        if (!defer_ok) {
+            pk = 1;
+        } else if (!p->tsmem) {
+            pk = 16;
+        } else {
+            Plan p1, p4;
+            const int r1 = make_plan(h, replicas, wpr, 1, &p1, reserve, cupim);
+            const int r4 = make_plan(h, replicas, wpr, 4, &p4, reserve, cupim);
+            if (r4 == PDIT_OK && (r1 != PDIT_OK || resident(p4, replicas) >= resident(p1, replicas))) {
+                *p = p4;
+                return PDIT_OK;
+            }
+            if (r1 != PDIT_OK) return r1;
+            *p = p1;
+            return PDIT_OK;
         }
     }
     p->pk = pk;
