@@ -15,6 +15,11 @@ N > 1: one process per GPU (torchrun); rank r runs replicas r*R..(r+1)*R-1
 (weak scaling, no collective in the timed region); value = all ranks'
 updates / max-over-ranks time.
 --impl reference: the CPU oracle on this host's cores (rank 0 only).
+
+Other workloads: --workload n100a (general form), c256 (two-level flow),
+n256 (largest size), dense --dense-n N, n30, n12; --mode cupim (concurrent
+updates); --workload ragged (time to 1% gap, batched vs one launch per
+instance); --workload served (continuous batching: capacity, p50/p99).
 """
 
 from __future__ import annotations

@@ -347,7 +347,8 @@ def pdit_set_pending_swaps(q: Qap, k: int):
 
 def pdit_autotune(q: Qap, replicas: int, beta, sweeps: int) -> tuple[int, int]:
     """Time the valid shapes on a short run (beta: CUDA float32 tensor of >= sweeps
-    values) and keep the fastest on the handle. Returns (warps per replica, pending swaps)."""
+    values) and keep the fastest on the handle. Returns (warps per replica, pending terms); the
+    placement and replicas per CTA it chose are in pdit_launch_shape."""
     out = np.zeros(2, dtype=np.int32)
     _check(lib().pdit_autotune(q.handle, replicas, ctypes.c_void_p(beta.data_ptr()), sweeps, _ptr(out)),
            "pdit_autotune")
