@@ -1207,6 +1207,9 @@ int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas,
 namespace {
 
 constexpr size_t kBatchStaticSmem = 512;
+// the multi-instance kernel's static shared memory: its descriptor and a unit index
+static_assert(sizeof(pdit::SweepArgs) + sizeof(int) + 16 <= kBatchStaticSmem,
+              "batch kernel descriptor exceeds the static shared-memory reserve");
 
 struct BatchOut {
     int32_t *perm;
