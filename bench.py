@@ -496,7 +496,7 @@ def main():
                     help="warps per replica (0: the library's choice)")
     ap.add_argument("--no-class-update", action="store_true",
                     help="run two-level-flow instances with the table kernels")
-    ap.add_argument("--mode", default="anneal", choices=["anneal", "cupim"],
+    ap.add_argument("--mode", default="anneal", choices=["anneal", "cupim", "pt"],
                     help="sequential p-dit sweeps (the paper's PIM) or concurrent updates (its CUPIM)")
     ap.add_argument("--pk", type=int, default=0,
                     help="pending rank-1 terms held before a table rewrite (0: the library's choice)")
@@ -554,8 +554,17 @@ def main():
         P.pdit_set_replicas_per_cta(q, args.rpc)
     if args.place:
         P.pdit_set_table_placement(q, args.place)
+    pt = args.mode == "pt"
+    ladder = 10
+    if pt:
+        # the paper's mode: sets of 10 rungs on a ladder from its beta-range
+        # selection (trial runs; untimed), exchange every 4 sweeps, timeout 100
+        replicas -= replicas % ladder
+        lo, hi, _ = P.pdit_beta_range(q)
+        beta = P.pdit_beta_ladder(lo, hi, ladder)
     shape = P.pdit_launch_shape(q, replicas)
-    beta = P.pdit_beta_schedule(kind, sweeps, P.pdit_beta_max(q))
+    if not pt:
+        beta = P.pdit_beta_schedule(kind, sweeps, P.pdit_beta_max(q))
     dev = torch.device("cuda", local)
     dbeta = torch.from_numpy(beta).to(dev)
     base = rank * replicas
@@ -566,8 +575,10 @@ def main():
             "replica_best_cost": torch.empty(replicas, dtype=torch.int64, device=dev),
             "replica_best_sweep": torch.empty(replicas, dtype=torch.int32, device=dev),
             "status": torch.zeros(1, dtype=torch.int32, device=dev)}
+    mode_code = {"anneal": P.PDIT_MODE_ANNEAL, "cupim": P.PDIT_MODE_CUPIM, "pt": P.PDIT_MODE_PT}[args.mode]
     o = P.opts(replicas=replicas, sweeps=sweeps, seed=0, replica_base=base, beta=dbeta.data_ptr(),
-               stream=stream.cuda_stream, mode=P.PDIT_MODE_CUPIM if args.mode == "cupim" else P.PDIT_MODE_ANNEAL)
+               stream=stream.cuda_stream, mode=mode_code, ladder_len=ladder if pt else 0,
+               exchange_period=4, timeout_periods=100)
     ws = torch.empty(P.pdit_workspace_bytes(q, o), dtype=torch.uint8, device=dev)
     o.workspace, o.workspace_bytes = ws.data_ptr(), ws.numel()
     for k, t in outs.items():
@@ -649,7 +660,8 @@ def main():
             eperm = torch.empty(n, dtype=torch.int32, device=dev)
             ecost = torch.empty(1, dtype=torch.int64, device=dev)
             eo = P.opts(replicas=replicas, sweeps=sweeps, seed=0, beta=ebeta.data_ptr(),
-                        stream=stream.cuda_stream, mode=P.PDIT_MODE_CUPIM,
+                        stream=stream.cuda_stream, mode=mode_code, ladder_len=ladder if pt else 0,
+                        exchange_period=4, timeout_periods=100,
                         best_perm=eperm.data_ptr(), best_cost=ecost.data_ptr())
             P.pdit_anneal_ex(qe, eo)
             rc = 0
@@ -713,10 +725,13 @@ def main():
                    "parallelism": "replicas sharded over %d GPU(s)" % world,
                    "l2": "flushed between timed steps (512 MiB write)",
                    "accept_fraction": accept_frac, "best_cost": best_cost, "launch": shape},
-        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n * n + 4 * sweeps,
+        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n * n + 4 * len(beta),
                 "d2h_bytes_per_step": 4 * n + 8 + 4,
                 "call": "qap_create + pdit_anneal + qap_destroy from pinned host buffers"},
-        "gpu_launches": 2 * args.steps,
+        # per step: sweep kernel + final reduction; PT mode: the rung set-up,
+        # one sweep kernel per exchange period (4 sweeps), one exchange kernel
+        # per completed period, the final reduction
+        "gpu_launches": args.steps * ((2 + -(-sweeps // 4) + sweeps // 4) if pt else 2),
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                    "reasons": clk.get("reasons"), "samples": clk.get("samples")},
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -730,7 +745,11 @@ def main():
                                     % (props.multi_processor_count, SMEM_BYTES_PER_CLK, sm_mhz)},
         "wall_s_timed_region": wall,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if pt:
+        line["config"]["beta"] = "ladder of %d rungs from the beta-range selection, exchange every 4 sweeps, " \
+                                 "top-rung timeout 100 periods; the CPU-baseline leg is omitted in this mode " \
+                                 "(the oracle splits work by whole ladders; PT parity is in the GPU tests)" % ladder
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not pt:
         gpu = {k: outs[k].cpu().numpy() for k in ("replica_best_cost", "replica_best_sweep", "replica_accepted")}
         line["cpu_baseline"] = cpu_baseline(D, F, beta, n, sweeps, args.mode, gpu)
     if rank == 0:
