@@ -2,6 +2,7 @@
 and its host-only logic (argument checks, beta schedules) behaves. No GPU."""
 
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -85,3 +86,27 @@ def test_beta_ladder_is_multiplicative(L):
         P.pdit_beta_ladder(0.0, 1.0, 10)
     with pytest.raises(P.PditError):
         P.pdit_beta_ladder(1.0, 0.5, 10)
+
+
+def test_header_compiles_as_c99_and_links(tmp_path, L):
+    """include/pdit.h is a plain C header: a C99 program that takes the
+    address of every declared function compiles and links against
+    libpdit.so (it is not run: there may be no GPU)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    names = P.header_functions()
+    src = tmp_path / "use_header.c"
+    body = "\n".join("    (void)&%s;" % n for n in names)
+    src.write_text('#include "pdit.h"\n#include <stdio.h>\nint main(void) {\n%s\n'
+                   '    printf("%%s\\n", pdit_strerror(PDIT_OK));\n    return 0;\n}\n' % body)
+    inc = os.path.join(os.path.dirname(P.HEADER))
+    libdir = os.path.dirname(P.LIB_PATH)
+    out = tmp_path / "use_header"
+    cmd = [gcc, "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(out), "-L", libdir, "-lpdit",
+           "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
