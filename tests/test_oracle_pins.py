@@ -480,3 +480,29 @@ def test_near_boundary_flag_on_constructed_draws():
                 assert O.choose(D, F, p, i, beta, r)[3] == 0
                 unflagged += 1
     assert flagged > 20 and unflagged > 20
+
+
+def test_reach_sweep_is_the_first_sweep_at_target():
+    """The target bookkeeping: a replica's recorded sweep s is the first at
+    which its best-so-far cost is at or below the target. Pinned by prefix
+    runs (the same per-sweep beta values truncated to s sweeps reproduce the
+    first s sweeps): after s + 1 sweeps the best is at or below the target,
+    after s sweeps it is not (-1 = already at the initial state)."""
+    D, F = G.named("n30")
+    beta = O.beta_schedule("linear", 40, O.beta_max(D, F))
+    full = O.anneal(D, F, beta, 40, 3, 0, 6, threads=6)
+    target = int(np.median(full["best_cost"]) * 1.02)
+    r = O.anneal(D, F, beta, 40, 3, 0, 6, threads=6, target=target)
+    checked = 0
+    for k in range(6):
+        s = int(r["reach_sweep"][k])
+        if s == 0x7FFFFFFF:
+            assert full["best_cost"][k] > target
+            continue
+        after = O.anneal(D, F, beta[:s + 1], s + 1, 3, k, k + 1)
+        assert after["best_cost"][0] <= target
+        if s >= 0:
+            before = O.anneal(D, F, beta[:s], s, 3, k, k + 1)
+            assert before["best_cost"][0] > target
+        checked += 1
+    assert checked >= 3
