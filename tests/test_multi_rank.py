@@ -74,3 +74,39 @@ def test_shard_ranges_cover_the_replica_space():
         base, cnt = multi.shard(r, 4, 10)
         seen.extend(range(base, base + cnt))
     assert seen == list(range(40))
+
+
+def _tie_main(rank, world, port, out_q):
+    import torch.distributed as dist
+
+    from paper_2605_24408_gb300 import multi
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        base, cnt = multi.shard(rank, world, 8)
+        # every rank reports the same best cost; rank r's winner is its local replica 5 - r
+        perm = np.arange(6, dtype=np.int32)[::-1] + rank
+        cost, gid, p = multi.global_best(42, 5 - rank, perm, base)
+        out_q.put((rank, cost, gid, p.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_ties_across_ranks_go_to_the_lowest_global_replica():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_tie_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, cost, gid, perm in results:
+        assert cost == 42
+        assert gid == 5  # rank 0's replica 5 (global 5) beats rank 1's replica 4 (global 12)
+        assert perm == list(np.arange(6)[::-1])
