@@ -720,7 +720,7 @@ def main():
                    if args.workload in WORKLOAD_TEXT else args.workload,
                    "mode": args.mode,
                    "update": "flow classes" if class_path else "table",
-                   "replicas_per_gpu": replicas, "sweeps": sweeps, "schedule": kind, "seed": 0,
+                   "replicas_per_gpu": replicas, "sweeps": sweeps, "schedule": "pt ladder" if pt else kind, "seed": 0,
                    "global_batch": replicas * world, "seq_len": n,
                    "parallelism": "replicas sharded over %d GPU(s)" % world,
                    "l2": "flushed between timed steps (512 MiB write)",
