@@ -1,0 +1,42 @@
+"""The bytes-per-update figures behind the bench line's roofline fractions,
+against hand-worked values (no GPU)."""
+
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_method_bytes_per_update():
+    # 4 (4 N) gathers + A (8 N^2 + 8 N): N = 100, A = 0.5 -> 1600 + 0.5 * 80800
+    assert bench.survey_bytes_per_update(100, 0.5) == pytest.approx(1600 + 40400)
+    # general form: four factor vectors, 16 N per accepted swap
+    assert bench.survey_bytes_per_update(100, 0.5, general=True) == pytest.approx(1600 + 0.5 * 81600)
+    assert bench.survey_bytes_per_update(256, 0.0) == 16 * 256
+
+
+def test_design_bytes_per_update():
+    n, dt, a = 100, 1, 0.25
+    # immediate: gather 16 N + 2 N dt; swap 8 N^2 + 4 N dt + 12 N
+    assert bench.algorithmic_bytes_per_update(n, dt, a, 1) == pytest.approx(
+        1600 + 200 + a * (80000 + 400 + 1200))
+    # 4 pending terms (one packed word): gather 16 N + 8 N + 2 N dt;
+    # swap 8 N^2 / 4 + 4 N dt + 16 N
+    assert bench.algorithmic_bytes_per_update(n, dt, a, 4) == pytest.approx(
+        1600 + 800 + 200 + a * (20000 + 400 + 1600))
+    # 16 pending terms (four packed words)
+    assert bench.algorithmic_bytes_per_update(n, dt, a, 16) == pytest.approx(
+        1600 + 3200 + 200 + a * (5000 + 400 + 1600))
+
+
+def test_flow_class_bytes_per_update():
+    # (17 + dt) N + A (2 N dt + 8 N)
+    assert bench.class_bytes_per_update(256, 1, 1.0) == pytest.approx(18 * 256 + 2 * 256 + 8 * 256)
+
+
+def test_shared_memory_peak_derivation():
+    # 152 SMs x 128 B/clk x 2070 MHz = 40.27 TB/s
+    assert 152 * bench.SMEM_BYTES_PER_CLK * 2070e6 / 1e9 == pytest.approx(40273.92)
