@@ -319,6 +319,22 @@ def test_cupim_matches_oracle(name, n, wpr, pk):
     check_equal(g, r, tables=True)
 
 
+@pytest.mark.parametrize("wpr,pk", [(0, 0), (1, 1), (1, 4), (2, 4)])
+def test_cupim_hand_worked_conflicts(wpr, pk):
+    """The hand-worked conflict case of the oracle's pins (N = 6, beta so
+    large that each location proposes its row's argmin): an energy-ordered
+    conflict, an equal-energy tie between two initiators and a pair proposed
+    from both ends; the GPU applies the same two swaps."""
+    from tests import test_oracle_cupim_rule as C
+
+    beta = np.array([C.BIG_BETA], np.float32)
+    g = gpu_run(C.D, C.F, beta, 1, C.SEED, 1, tables=True, wpr=wpr, pk=pk, mode=3)
+    r = O.anneal(C.D, C.F, beta, 1, C.SEED, 0, 1, mode="cupim", tables=True)
+    check_equal(g, r, tables=True)
+    assert g["replica_final_perm"][0].tolist() == C.EXPECTED
+    assert int(g["replica_accepted"][0]) == 2
+
+
 # --- launch-shape knobs and the autotuner ------------------------------------------
 
 @pytest.mark.parametrize("n,g", [(100, 1), (100, 3), (256, 1), (256, 3)])
