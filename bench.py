@@ -40,6 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2605_24408_gb300 import instances as G  # noqa: E402
+from paper_2605_24408_gb300 import multi  # noqa: E402
 
 WORKLOADS = {
     # name: (instance, replicas, sweeps, schedule)
@@ -503,6 +504,9 @@ def main():
     ap.add_argument("--rpc", type=int, default=0,
                     help="replicas per CTA at most (0: the library's choice)")
     ap.add_argument("--dense-n", type=int, default=180, help="size of the 'dense' workload")
+    ap.add_argument("--influence", default="auto", choices=["auto", "table", "products"],
+                    help="influence entries: the library's choice, the incrementally updated table, "
+                         "or dot products of byte rows (no table)")
     ap.add_argument("--place", type=int, default=0, choices=[0, 1, 2],
                     help="influence tables: 0 library's choice, 1 shared memory, 2 global memory")
     ap.add_argument("--sweeps", type=int, default=0,
@@ -554,6 +558,9 @@ def main():
         P.pdit_set_replicas_per_cta(q, args.rpc)
     if args.place:
         P.pdit_set_table_placement(q, args.place)
+    infl = {"auto": P.PDIT_INFLUENCE_AUTO, "table": P.PDIT_INFLUENCE_TABLE,
+            "products": P.PDIT_INFLUENCE_PRODUCTS}[args.influence]
+    P.pdit_set_influence(q, infl)
     pt = args.mode == "pt"
     ladder = 10
     if pt:
@@ -626,10 +633,10 @@ def main():
 
     # final answer over ranks (outside the timed region)
     best_cost = int(outs["best_cost"].item())
+    rep_best = outs["replica_best_cost"].cpu().numpy()
+    best_replica = base + multi.rank_winner(rep_best)
     if dist is not None:
-        from paper_2605_24408_gb300 import multi
-
-        best_cost, _, _ = multi.global_best(best_cost, 0, outs["best_perm"].cpu().numpy(), base, dev)
+        best_cost, best_replica, _ = multi.rank_result(rep_best, outs["best_perm"].cpu().numpy(), base, dev)
 
     # end to end, the whole user call per step: qap_create (H2D of D and F from
     # host memory), pdit_anneal (H2D of beta, D2H of the result), qap_destroy
@@ -645,7 +652,8 @@ def main():
         t0 = time.perf_counter()
         qe = P.qap_create_host_ptrs(n, hD.data_ptr(), hF.data_ptr())
         for setter, v in ((P.pdit_set_warps_per_replica, args.wpr), (P.pdit_set_pending_swaps, args.pk),
-                          (P.pdit_set_replicas_per_cta, args.rpc), (P.pdit_set_table_placement, args.place)):
+                          (P.pdit_set_replicas_per_cta, args.rpc), (P.pdit_set_table_placement, args.place),
+                          (P.pdit_set_influence, infl)):
             if v:
                 setter(qe, v)
         if args.no_class_update:
@@ -724,7 +732,8 @@ def main():
                    "global_batch": replicas * world, "seq_len": n,
                    "parallelism": "replicas sharded over %d GPU(s)" % world,
                    "l2": "flushed between timed steps (512 MiB write)",
-                   "accept_fraction": accept_frac, "best_cost": best_cost, "launch": shape},
+                   "accept_fraction": accept_frac, "best_cost": best_cost, "best_replica": best_replica,
+                   "launch": shape},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n * n + 4 * len(beta),
                 "d2h_bytes_per_step": 4 * n + 8 + 4,
                 "call": "qap_create + pdit_anneal + qap_destroy from pinned host buffers"},

@@ -140,12 +140,49 @@ int pdit_set_replicas_per_cta(pdit_qap *h, int g);
  * pdit_launch_shape -- the sweep-kernel launch a call with `replicas` chains
  * would use: shape[0] warps per replica, [1] candidates per thread, [2]
  * replicas per CTA, [3] CTAs, [4] 1 if the influence tables live in shared
- * memory (0: global memory), [5] dynamic shared memory bytes per CTA.
+ * memory (0: global memory; 2: no table, the dot-product kernel of
+ * pdit_set_influence), [5] dynamic shared memory bytes per CTA.
  * [6] pending rank-1 terms held before the influence table is rewritten (1 =
  * after each swap; 4 or 16).
  * `shape` is a host array of 7 ints. Errors: PDIT_EINVAL, PDIT_ENOTSUP.
  */
 int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape);
+
+/* Influence entries (pdit_set_influence). */
+#define PDIT_INFLUENCE_AUTO 0     /* dot products where eligible and no table knob is set, else the table */
+#define PDIT_INFLUENCE_TABLE 1    /* the influence table of Eq. 2, updated after every accepted swap */
+#define PDIT_INFLUENCE_PRODUCTS 2 /* dot products of byte rows of D and of the permuted F (no table) */
+
+/*
+ * pdit_set_influence -- how later sequential-mode calls on this handle obtain
+ * the two influence entries each swap energy needs (Eq. 3 in the one-term
+ * units: I[i][p(j)] and I[j][p(i)], I[m][c] = sum_y D[m][y] F[c][p(y)]).
+ *   PDIT_INFLUENCE_TABLE    : keep every replica's N x N int32 table and add
+ *                             the rank-1 change of Eq. 2 after each accepted
+ *                             swap (the paper's incremental scheme; the table
+ *                             knobs above apply).
+ *   PDIT_INFLUENCE_PRODUCTS : keep instead the flow matrix permuted to
+ *                             location order, Q[x][y] = F[p(x)][p(y)] (N x N
+ *                             bytes), and form both entries as 8-bit dot
+ *                             products I[i][p(j)] = D[i] . Q[j], I[j][p(i)] =
+ *                             D[j] . Q[i]; an accepted swap exchanges two rows
+ *                             and two columns of Q and updates the p-diagonal
+ *                             h[x] = I[x][p(x)] incrementally. Symmetric
+ *                             instances whose D and F entries all lie in
+ *                             -128..127, in the sequential modes, without
+ *                             the table dump (PDIT_ENOTSUP otherwise, at the
+ *                             next call). Two-level-flow instances keep the
+ *                             flow-class kernel unless pdit_set_class_update
+ *                             turns it off.
+ *   PDIT_INFLUENCE_AUTO     : products where eligible, unless a table knob
+ *                             (pending swaps, placement) is set; the table
+ *                             otherwise (also for the concurrent-update mode,
+ *                             for calls that dump the tables, and for sizes
+ *                             with no compiled product shape).
+ * The entries are the same exact integers either way, so results do not
+ * depend on the choice. Errors: PDIT_EINVAL.
+ */
+int pdit_set_influence(pdit_qap *h, int mode);
 
 /* Instance forms (pdit_instance_form). */
 #define PDIT_FORM_SYMMETRIC 0     /* D, F symmetric: one-term table I (Eq. 2 = -2 I) */
@@ -258,7 +295,9 @@ void pdit_opts_init(pdit_opts *o);
 
 /*
  * pdit_workspace_bytes -- device scratch needed by pdit_anneal_ex for the
- * given options (replicas, mode, ladder). Returns 0 for invalid input.
+ * given options (replicas, mode, ladder, and whether `tables` is requested,
+ * which selects the table kernels): query it with the options of the call.
+ * Returns 0 for invalid input.
  * The workspace holds every replica's state between calls (permutation,
  * energy, best-so-far, counters, and in PT mode the influence tables), so a
  * call with PDIT_FLAG_RESUME continues exactly where the previous one
@@ -307,25 +346,35 @@ int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out);
  *              max|D| max|F| < 2^31 (not checked here).
  *   replicas, beta (DEVICE, `sweeps` floats), sweeps, seed: as pdit_anneal.
  *   best_perm (DEVICE, n int32), best_cost (DEVICE, 1 int64): outputs.
+ *   status   : DEVICE, 1 int32, or NULL: the PDIT_STATUS_* audit bits of
+ *              the call (0 when every audit passed), as pdit_opts.status.
+ *              With NULL the audit result is not reported.
  *   stream   : cudaStream_t (NULL = legacy default stream); asynchronous.
  * Replica ids are 0..replicas-1, instance id 0: the results equal those of
  * pdit_anneal / pdit_anneal_ex with the same arguments.
  * The per-replica state lives in one static device array of
- * PDIT_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps until
- * exit. A call needs about replicas * (8 n + 36) bytes of it; larger calls
- * return PDIT_ENOMEM. The staged matrices must fit shared memory with one
- * replica table (n <= 150 or so): PDIT_ENOTSUP otherwise.
+ * PDIT_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU loading this library
+ * keeps until exit. A call needs replicas * (8 n + 32) bytes of it plus at
+ * most 3 KiB (each of its eleven arrays starts on a 256-byte boundary);
+ * larger calls return PDIT_ENOMEM. The staged matrices must fit shared
+ * memory with one replica table (n <= 150 or so): PDIT_ENOTSUP otherwise.
  * Every call shares the array and it keeps the last call's contents: calls
  * that overlap on the GPU (different streams, or host threads) race on it;
- * serialise them. The first call on each device looks up the array's device
- * address with that device current; make that first call before any stream
- * capture.
+ * serialise them.
+ * First call on each device: CUDA loads this library's device code lazily
+ * (the default since CUDA 12.2), so the first call on a device is the one
+ * that places the 8 MiB array there, and it also looks up the array's
+ * device address with that device current. A process that must not grow
+ * its footprint later should make one call at start-up (or run with
+ * CUDA_MODULE_LOADING=EAGER), and make that first call before any stream
+ * capture. The address is kept for the life of the process: after a
+ * cudaDeviceReset, calls on that device are not supported.
  * Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ENOTSUP, PDIT_ECUDA.
  */
 #define PDIT_NOALLOC_SCRATCH_BYTES (8u << 20)
 int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas, const float *beta,
                         int sweeps, uint64_t seed, int32_t *best_perm, int64_t *best_cost,
-                        void *stream);
+                        int32_t *status, void *stream);
 
 /*
  * pdit_beta_range -- the paper's beta-range selection (Implementation
@@ -496,6 +545,23 @@ int pdit_read_qaplib_solution(const char *path, int *n, int64_t *cost, int32_t *
  * permutation of 0..n-1, n out of range, NULL), PDIT_EIO.
  */
 int pdit_write_qaplib_solution(const char *path, int n, int64_t cost, const int32_t *perm);
+
+/*
+ * pdit_probe_peaks -- measure, on the current device, the on-chip peaks that
+ * bound the sweep kernels (the denominators of their rooflines; the paper
+ * reports none): one CTA of 1024 threads per SM, timed with CUDA events and
+ * with SM cycles (clock64).
+ *   iters : loop trips of each probe (>= 1; 2000 takes a few milliseconds).
+ *   out   : host array of 6 doubles:
+ *           [0] shared-memory load bandwidth, bytes/s over all SMs
+ *               (conflict-free 128-bit ld.shared, 512 contiguous bytes per warp);
+ *           [1] the same in bytes per SM clock per SM;
+ *           [2] dp4a.s32.s32 thread-operations/s over all SMs;  [3] per SM clock per SM;
+ *           [4] mad.lo.s32 thread-operations/s over all SMs;    [5] per SM clock per SM.
+ * Synchronous on a private stream; allocates and frees two small device
+ * buffers. Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ECUDA.
+ */
+int pdit_probe_peaks(int iters, double *out);
 
 /* pdit_strerror -- static text for an error code. */
 const char *pdit_strerror(int code);

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpdit.so")
 
 SOURCES = ["pdit_host.cu", "pdit_io.cu", "pdit_class.cu", "pdit_sweep_i8.cu", "pdit_sweep_i16.cu", "pdit_sweep_i32.cu",
-           "pdit_sweep_gen_i8.cu", "pdit_sweep_gen_i16.cu", "pdit_sweep_gen_i32.cu"]
+           "pdit_sweep_gen_i8.cu", "pdit_sweep_gen_i16.cu", "pdit_sweep_gen_i32.cu", "pdit_peaks.cu", "pdit_dot.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

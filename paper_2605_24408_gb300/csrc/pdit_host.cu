@@ -44,6 +44,7 @@ struct pdit_qap {
     int force_pk = 0;       // pending swaps before a table rewrite; 0 = chosen per launch
     int force_groups = 0;   // replicas per CTA; 0 = chosen per launch
     int force_place = 0;    // influence tables: 0 = shared memory when they fit, 1 = shared, 2 = global
+    int force_infl = 0;     // influence entries: PDIT_INFLUENCE_AUTO, _TABLE or _PRODUCTS
 };
 
 namespace {
@@ -91,7 +92,7 @@ int stage_stride(int n, int dt) {
 
 struct Plan {
     int maxk = 1, wpr = 1, pk = 1;
-    bool tsmem = true, cls = false;
+    bool tsmem = true, cls = false, dot = false;
     int stride = 0, sv_len = 0, cupim_off = 0, v2_off = 0, rc_off = 0, dstride = 0;
     size_t table_elems = 0;  // int32 entries of one replica's saved table (workspace)
     size_t df_bytes = 0, group_bytes = 0, smem = 0;
@@ -288,6 +289,81 @@ int class_launch(int dt, const Plan &p, const pdit::SweepArgs &a, cudaStream_t s
     return pdit::class_launch<int32_t>(p.maxk, p.wpr, a, p.grid, p.threads, p.smem, st);
 }
 
+// Launch shape of the dot-product kernel (pdit_dot.cu): D as int8 in slot
+// order once per CTA, then per replica group: scratch, the permuted flow
+// matrix Q (rows x stride bytes), p and h. Row stride: 16 bytes x odd.
+int make_dot_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
+    const int n = h->n;
+    const int cover = cover_for(n);
+    const int npad = (n + 3) & ~3;
+    int s16 = (n + 15) / 16;
+    if (s16 % 2 == 0) s16 += 1;
+    p->dot = true;
+    p->tsmem = true;
+    p->pk = 1;
+    p->stride = 16 * s16;
+    p->dstride = n;
+    p->table_elems = 0;
+    p->sv_len = 0;
+    const size_t budget = h->smem_optin;
+    auto sizes = [&](int maxk, size_t *df, size_t *grp) {
+        const size_t rows = (size_t)((n + maxk - 1) / maxk) * maxk;
+        *df = rows * p->stride;
+        *grp = align_up(pdit::kScratchBytes + rows * p->stride + (size_t)8 * npad, 16);
+    };
+    auto fit_for = [&](int w) {
+        size_t df, grp;
+        sizes(cover / (32 * w), &df, &grp);
+        return df + grp > budget ? 0 : (int)((budget - df) / grp);
+    };
+    if (wpr <= 0) {
+        // the fewest warps per replica that keep about 16 warps resident per
+        // SM, among the compiled shapes; else the shape with the most
+        int best = 0, best_warps = -1;
+        for (int w = 1; w <= cover / 32; w <<= 1) {
+            if (!pdit::dot_shape_compiled(cover / (32 * w), w)) continue;
+            int g = std::min(fit_for(w), pdit::dot_bound(cover / (32 * w), w) / (32 * w));
+            if (w > 1) g = std::min(g, 15);
+            if (g * w >= 16) {
+                best = w;
+                break;
+            }
+            if (g * w > best_warps) {
+                best = w;
+                best_warps = g * w;
+            }
+        }
+        if (!best) return PDIT_ENOTSUP;
+        wpr = best;
+    }
+    if (wpr < 1 || wpr > cover / 32 || (wpr & (wpr - 1))) return PDIT_EINVAL;
+    p->wpr = wpr;
+    p->maxk = cover / (32 * wpr);
+    if (!pdit::dot_shape_compiled(p->maxk, wpr)) return PDIT_ENOTSUP;
+    sizes(p->maxk, &p->df_bytes, &p->group_bytes);
+    if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
+    const int fit = (int)((budget - p->df_bytes) / p->group_bytes);
+    int g = std::min(fit, pdit::dot_bound(p->maxk, wpr) / (32 * wpr));
+    if (wpr > 1) g = std::min(g, 15);  // named barriers 1..15
+    if (h->force_groups > 0) g = std::min(g, h->force_groups);
+    const int per_sm = (replicas + h->num_sms - 1) / h->num_sms;
+    g = std::max(1, std::min(g, per_sm));
+    p->groups = g;
+    p->threads = 32 * wpr * g;
+    p->smem = p->df_bytes + (size_t)g * p->group_bytes;
+    int bps = 0;
+    const int e = pdit::dot_blocks_per_sm(p->maxk, wpr, p->threads, p->smem, &bps);
+    if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
+    if (bps < 1) bps = 1;
+    const int need = (replicas + g - 1) / g;
+    p->grid = std::max(1, std::min(need, h->num_sms * bps));
+    return PDIT_OK;
+}
+
+// Whether an instance can run the dot-product kernel: symmetric, every entry
+// of D and F in a signed byte (dp4a operands).
+bool dot_eligible(const pdit_qap *h) { return !h->asym && h->dt_bytes == 1; }
+
 // Whether a call runs the flow-class kernel: a two-level-flow instance with
 // the path enabled, in a sequential mode, without a request for the N x N
 // table dump (which only the table kernels keep).
@@ -295,9 +371,27 @@ bool use_class_path(const pdit_qap *h, const pdit_opts *o) {
     return h->cls && h->use_cls && o->mode != PDIT_MODE_CUPIM && !o->tables;
 }
 
-// Launch plan of a call: the flow-class kernel or the table kernels.
+// Whether a call runs the dot-product kernel: an eligible instance in a
+// sequential mode, without a request for the table dump or for table-kernel
+// knobs (pending terms, table placement), unless the handle asks for it.
+bool use_dot_path(const pdit_qap *h, const pdit_opts *o) {
+    if (!dot_eligible(h) || o->mode == PDIT_MODE_CUPIM || o->tables) return false;
+    return h->force_infl == PDIT_INFLUENCE_AUTO && h->force_pk == 0 && h->force_place == PDIT_PLACE_AUTO;
+}
+
+// Launch plan of a call: the flow-class kernel, the dot-product kernel or
+// the table kernels.
 int plan_for(const pdit_qap *h, const pdit_opts *o, Plan *p) {
     if (use_class_path(h, o)) return make_class_plan(h, o->replicas, h->force_wpr, p);
+    if (h->force_infl == PDIT_INFLUENCE_PRODUCTS) {
+        if (!dot_eligible(h) || o->mode == PDIT_MODE_CUPIM || o->tables) return PDIT_ENOTSUP;
+        return make_dot_plan(h, o->replicas, h->force_wpr, p);
+    }
+    if (use_dot_path(h, o)) {
+        const int rc = make_dot_plan(h, o->replicas, h->force_wpr, p);
+        if (rc != PDIT_ENOTSUP) return rc;
+        *p = Plan();  // no dot shape for this size or mapping: the table kernels
+    }
     return make_plan(h, o->replicas, h->force_wpr, h->force_pk, p, 0, o->mode == PDIT_MODE_CUPIM);
 }
 
@@ -307,7 +401,7 @@ struct Workspace {
     size_t bytes;
 };
 
-bool needs_tables(const pdit_opts *o, const Plan &p) { return o->mode == PDIT_MODE_PT || !p.tsmem; }
+bool needs_tables(const pdit_opts *o, const Plan &p) { return !p.dot && (o->mode == PDIT_MODE_PT || !p.tsmem); }
 
 Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base) {
     const size_t R = (size_t)o->replicas, n = (size_t)h->n;
@@ -649,14 +743,16 @@ int pdit_set_warps_per_replica(pdit_qap *h, int wpr) {
 int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape) {
     if (!h || replicas < 1 || !shape) return PDIT_EINVAL;
     Plan p;
-    const int rc = (h->cls && h->use_cls) ? make_class_plan(h, replicas, h->force_wpr, &p)
-                                          : make_plan(h, replicas, h->force_wpr, h->force_pk, &p);
+    pdit_opts o;
+    pdit_opts_init(&o);
+    o.replicas = replicas;
+    const int rc = plan_for(h, &o, &p);
     if (rc) return rc;
     shape[0] = p.wpr;
     shape[1] = p.maxk;
     shape[2] = p.groups;
     shape[3] = p.grid;
-    shape[4] = p.tsmem ? 1 : 0;
+    shape[4] = p.dot ? 2 : (p.tsmem ? 1 : 0);
     shape[5] = (int)p.smem;
     shape[6] = p.pk;
     return PDIT_OK;
@@ -683,6 +779,12 @@ int pdit_set_table_placement(pdit_qap *h, int place) {
 int pdit_set_replicas_per_cta(pdit_qap *h, int g) {
     if (!h || g < 0) return PDIT_EINVAL;
     h->force_groups = g;
+    return PDIT_OK;
+}
+
+int pdit_set_influence(pdit_qap *h, int mode) {
+    if (!h || mode < PDIT_INFLUENCE_AUTO || mode > PDIT_INFLUENCE_PRODUCTS) return PDIT_EINVAL;
+    h->force_infl = mode;
     return PDIT_OK;
 }
 
@@ -778,12 +880,13 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.fresh = (!resume && first) ? 1 : 0;
         // Tables persist across segments in PT mode; the global-table path
         // always works in place.
-        a.table_in = (pt && !(first && !resume)) || (!plan.tsmem && !a.fresh && pt) ? 1 : 0;
-        a.table_out = pt ? 1 : 0;
+        a.table_in = !plan.dot && ((pt && !(first && !resume)) || (!plan.tsmem && !a.fresh && pt)) ? 1 : 0;
+        a.table_out = !plan.dot && pt ? 1 : 0;
         a.dump = (next == se) ? o->tables : nullptr;
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
             const int e = plan.cls ? class_launch(h->dt_bytes, plan, a, st)
+                        : plan.dot ? pdit::dot_launch(plan.maxk, plan.wpr, a, plan.grid, plan.threads, plan.smem, st)
                                    : sweep_launch(h->dt_bytes, h->asym != 0, plan, a, st);
             if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
         }
@@ -1093,7 +1196,9 @@ int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out) {
 // pdit_anneal_ex keeps in a workspace) is this file-scope device array, so
 // the call never allocates device memory. In host code `g_noalloc_scratch`
 // names a host-side stand-in, not a device address: the address is taken
-// with cudaGetSymbolAddress once per device, with that device current.
+// with cudaGetSymbolAddress once per device, with that device current, at
+// the first call on that device, and kept for the life of the process (a
+// device reset would move the array; calls after one are not supported).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1122,7 +1227,7 @@ extern "C" {
 
 int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas, const float *beta,
                         int sweeps, uint64_t seed, int32_t *best_perm, int64_t *best_cost,
-                        void *stream) {
+                        int32_t *status, void *stream) {
     if (n < 2 || n > PDIT_N_MAX || !D || !F || replicas < 1 || sweeps < 0) return PDIT_EINVAL;
     if (!best_perm || !best_cost || (sweeps > 0 && !beta)) return PDIT_EINVAL;
     if ((uint64_t)sweeps >= 0xFFFFFFFFull) return PDIT_EINVAL;
@@ -1193,8 +1298,9 @@ int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas,
     a.sv_len = plan.sv_len;
     const int e = sweep_launch(4, false, plan, a, st);
     if (e != 0) return cuda_fail((cudaError_t)e, "sweep kernel launch");
+    // the audit bits reach the caller through `status` when given
     finalize_kernel<<<1, 1024, 0, st>>>(replicas, n, w.best_energy, w.best_perm, best_perm, best_cost,
-                                        w.status, nullptr);
+                                        w.status, status);
     PDIT_CK(cudaGetLastError());
     return PDIT_OK;
 }

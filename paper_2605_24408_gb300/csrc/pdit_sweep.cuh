@@ -248,23 +248,22 @@ __device__ __forceinline__ void fisher_yates(const SweepArgs &a, uint32_t grep, 
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 5 draw over the n outcomes whose swap energies the group has written to
-// sv[0..n) (with one candidate per thread, MAXK = 1, each thread passes its
-// own energy in dself and its location's facility in pself instead, and sv is
-// not read; lmin: the minimum over this thread's own candidates): group
-// minimum, binary32 weights of the shifted energies, thread-contiguous 64-bit
-// prefix sums (thread t holds outcomes t*MAXK .. t*MAXK + MAXK - 1), the
-// 64-bit draw scaled by the total, and the first outcome whose inclusive
-// prefix sum exceeds it. Returns (chosen location js, its energy change,
-// sp[js]), the same on every thread of the group; sp[js] is read by the
-// owning thread before the final synchronisation, so the caller may rewrite
-// sp once every thread has returned. Ends with the group synchronised, so sv
-// may be rewritten afterwards.
+// Eq. 5 draw over n outcomes held thread-contiguously: thread t holds the
+// swap energies of outcomes t*MAXK + k (k < MAXK; outcomes >= n are ignored),
+// which `load(dc)` fills in once the group minimum is known (so energies that
+// other threads wrote to shared memory are read after the synchronisation of
+// the minimum), and `fac(k)` gives the facility at outcome t*MAXK + k (called
+// on the owning thread only); lmin is the minimum over this thread's own
+// outcomes. Group minimum, binary32 weights of the shifted energies, 64-bit
+// prefix sums in outcome order, the 64-bit draw scaled by the total, and the
+// first outcome whose inclusive prefix sum exceeds it. Returns (chosen
+// location js, its energy change, the facility at js), the same on every
+// thread of the group; the facility is read by the owning thread before the
+// final synchronisation. Ends with the group synchronised.
 // ---------------------------------------------------------------------------
-template <int MAXK, int WPR>
-__device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, int n, int t, int lmin,
-                                         int dself, int pself, float beta, unsigned long long draw,
-                                         int bar, GroupScratch *gs) {
+template <int MAXK, int WPR, typename Load, typename Fac>
+__device__ __forceinline__ int3 eq5_draw_core(Load load, Fac fac, int n, int t, int lmin, float beta,
+                                              unsigned long long draw, int bar, GroupScratch *gs) {
     const int lane = t & 31;
     const int wg = t >> 5;
     int dmin = __reduce_min_sync(kFull, lmin);
@@ -280,10 +279,7 @@ __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, i
 
     // ---- sample: thread-contiguous weights, 64-bit prefix sums
     int dc[MAXK];
-    if constexpr (MAXK == 1)
-        dc[0] = dself;
-    else
-        load_block<MAXK>(sv, t, dc);
+    load(dc);
     unsigned long long pre[MAXK];
     unsigned long long lsum = 0;
 #pragma unroll
@@ -326,10 +322,7 @@ __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, i
         for (int k = 0; k < MAXK; ++k)
             if (k == kk) dsel = dc[k];
         jloc = t * MAXK + kk;
-        if constexpr (MAXK == 1)
-            fsel = pself;
-        else
-            fsel = sp[jloc];
+        fsel = fac(kk);
     }
     int js, dstar, fb;
     if constexpr (WPR > 1) {
@@ -348,6 +341,37 @@ __device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, i
         __syncwarp();
     }
     return make_int3(js, dstar, fb);
+}
+
+// The draw over energies that each thread holds in registers for its own
+// outcomes t*MAXK + k.
+template <int MAXK, int WPR, typename Fac>
+__device__ __forceinline__ int3 eq5_draw_regs(const int (&dc)[MAXK], Fac fac, int n, int t, int lmin, float beta,
+                                              unsigned long long draw, int bar, GroupScratch *gs) {
+    auto load = [&](int (&o)[MAXK]) {
+#pragma unroll
+        for (int k = 0; k < MAXK; ++k) o[k] = dc[k];
+    };
+    return eq5_draw_core<MAXK, WPR>(load, fac, n, t, lmin, beta, draw, bar, gs);
+}
+
+// The draw over energies the group has written to sv[0..n) in location
+// order (with one candidate per thread, MAXK = 1, each thread passes its own
+// energy in dself and its location's facility in pself instead, and sv is
+// not read). The facility of the drawn location is read from sp by its
+// owner, so the caller may rewrite sp once every thread has returned.
+template <int MAXK, int WPR>
+__device__ __forceinline__ int3 eq5_draw(const int32_t *sv, const int32_t *sp, int n, int t, int lmin,
+                                         int dself, int pself, float beta, unsigned long long draw,
+                                         int bar, GroupScratch *gs) {
+    auto load = [&](int (&o)[MAXK]) {
+        if constexpr (MAXK == 1)
+            o[0] = dself;
+        else
+            load_block<MAXK>(sv, t, o);
+    };
+    auto fac = [&](int kk) { return MAXK == 1 ? pself : sp[t * MAXK + kk]; };
+    return eq5_draw_core<MAXK, WPR>(load, fac, n, t, lmin, beta, draw, bar, gs);
 }
 
 // Bytes of packed word w that hold one of the np pending terms (4 per word).
@@ -1392,5 +1416,16 @@ int class_launch(int maxk, int wpr, const SweepArgs &a, int grid, int threads, s
 __host__ __device__ constexpr int class_bound(int maxk, int wpr) {
     return maxk >= 4 ? 512 : 1024;
 }
+
+// Dot-product sweep kernels (pdit_dot.cu): symmetric instances with every
+// entry of D and F in a signed byte; no influence table, a permuted copy of F
+// per replica (see that file). Shapes (MAXK, WPR) listed there. Return a
+// cudaError_t value; cudaErrorInvalidValue for a shape with no kernel.
+__host__ __device__ constexpr int dot_bound(int maxk, int wpr) {
+    return maxk == 1 ? (wpr == 1 ? 1024 : 512) : maxk == 2 ? 640 : maxk == 4 ? 512 : 384;
+}
+bool dot_shape_compiled(int maxk, int wpr);
+int dot_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks);
+int dot_launch(int maxk, int wpr, const SweepArgs &a, int grid, int threads, size_t smem, cudaStream_t stream);
 
 }  // namespace pdit

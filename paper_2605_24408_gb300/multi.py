@@ -35,3 +35,18 @@ def global_best(best_cost: int, best_replica: int, perm, replica_base: int, devi
     p = torch.as_tensor(np.ascontiguousarray(perm, dtype=np.int32), device=dev)
     dist.broadcast(p, src=wrank)
     return cost, wid, p.cpu().numpy()
+
+
+def rank_winner(replica_best_cost) -> int:
+    """This rank's winning replica (its index within the rank): the smallest
+    best cost, ties to the lowest index."""
+    c = np.asarray(replica_best_cost, dtype=np.int64)
+    return int(np.argmin(c))  # argmin returns the first of equal minima
+
+
+def rank_result(replica_best_cost, best_perm, replica_base: int, device=None):
+    """The final answer of a sharded run from one rank's per-replica best
+    costs and its best permutation (the permutation of its winning replica):
+    (cost, global replica id, perm) agreed by every rank."""
+    w = rank_winner(replica_best_cost)
+    return global_best(int(np.asarray(replica_best_cost)[w]), w, best_perm, replica_base, device)

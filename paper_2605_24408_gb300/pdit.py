@@ -29,6 +29,9 @@ PDIT_EIO = -7
 PDIT_PLACE_AUTO = 0
 PDIT_PLACE_SHARED = 1
 PDIT_PLACE_GLOBAL = 2
+PDIT_INFLUENCE_AUTO = 0
+PDIT_INFLUENCE_TABLE = 1
+PDIT_INFLUENCE_PRODUCTS = 2
 PDIT_FORM_SYMMETRIC = 0
 PDIT_FORM_GENERAL = 1
 PDIT_FORM_FLOW_CLASSES = 2
@@ -138,6 +141,8 @@ def lib():
     L.pdit_set_warps_per_replica.restype = ctypes.c_int
     L.pdit_launch_shape.argtypes = [vp, ctypes.c_int, vp]
     L.pdit_launch_shape.restype = ctypes.c_int
+    L.pdit_set_influence.argtypes = [vp, ctypes.c_int]
+    L.pdit_set_influence.restype = ctypes.c_int
     L.pdit_set_pending_swaps.argtypes = [vp, ctypes.c_int]
     L.pdit_set_pending_swaps.restype = ctypes.c_int
     L.pdit_beta_range.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -146,10 +151,12 @@ def lib():
     L.pdit_beta_ladder.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     L.pdit_beta_ladder.restype = ctypes.c_int
     L.pdit_anneal_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_uint64,
-                                      vp, vp, vp]
+                                      vp, vp, vp, vp]
     L.pdit_anneal_noalloc.restype = ctypes.c_int
     L.pdit_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp]
     L.pdit_autotune.restype = ctypes.c_int
+    L.pdit_probe_peaks.argtypes = [ctypes.c_int, vp]
+    L.pdit_probe_peaks.restype = ctypes.c_int
     L.pdit_batch_create.argtypes = [ctypes.POINTER(pdit_batch_item), ctypes.c_int, ctypes.c_uint32,
                                     ctypes.POINTER(vp)]
     L.pdit_batch_create.restype = ctypes.c_int
@@ -341,6 +348,10 @@ def pdit_set_replicas_per_cta(q: Qap, g: int):
     _check(lib().pdit_set_replicas_per_cta(q.handle, g), "pdit_set_replicas_per_cta")
 
 
+def pdit_set_influence(q: Qap, mode: int):
+    _check(lib().pdit_set_influence(q.handle, mode), "pdit_set_influence")
+
+
 def pdit_set_pending_swaps(q: Qap, k: int):
     _check(lib().pdit_set_pending_swaps(q.handle, k), "pdit_set_pending_swaps")
 
@@ -356,10 +367,16 @@ def pdit_autotune(q: Qap, replicas: int, beta, sweeps: int) -> tuple[int, int]:
 
 
 def pdit_launch_shape(q: Qap, replicas: int) -> dict:
+    """The launch a call would use; 'influence' says whether it keeps the
+    influence tables ('table') or forms the entries by dot products
+    ('products', no table)."""
     out = np.zeros(7, dtype=np.int32)
     _check(lib().pdit_launch_shape(q.handle, replicas, _ptr(out)), "pdit_launch_shape")
-    return dict(zip(["warps_per_replica", "candidates_per_thread", "replicas_per_cta", "ctas",
-                     "tables_in_smem", "smem_bytes", "pending_swaps"], (int(x) for x in out)))
+    d = dict(zip(["warps_per_replica", "candidates_per_thread", "replicas_per_cta", "ctas",
+                  "tables_in_smem", "smem_bytes", "pending_swaps"], (int(x) for x in out)))
+    d["influence"] = "products" if d["tables_in_smem"] == 2 else "table"
+    d["tables_in_smem"] = 1 if d["tables_in_smem"] == 1 else 0
+    return d
 
 
 def pdit_beta_max(q: Qap) -> float:
@@ -385,6 +402,16 @@ def pdit_beta_ladder(beta_lo: float, beta_hi: float, length: int = 10) -> np.nda
     return out
 
 
+def pdit_probe_peaks(iters: int = 2000) -> dict:
+    """On-chip peaks of the current device (shared-memory load bandwidth,
+    dp4a and 32-bit multiply-add rates), per second and per SM clock per SM."""
+    out = np.zeros(6, dtype=np.float64)
+    _check(lib().pdit_probe_peaks(iters, _ptr(out)), "pdit_probe_peaks")
+    return {"smem_bytes_per_s": float(out[0]), "smem_bytes_per_clk_sm": float(out[1]),
+            "dp4a_ops_per_s": float(out[2]), "dp4a_ops_per_clk_sm": float(out[3]),
+            "imad_ops_per_s": float(out[4]), "imad_ops_per_clk_sm": float(out[5])}
+
+
 def pdit_beta_schedule(kind: str, sweeps: int, beta_max: float) -> np.ndarray:
     out = np.zeros(max(sweeps, 1), dtype=np.float32)
     _check(lib().pdit_beta_schedule({"linear": 0, "geometric": 1}[kind], sweeps, beta_max, _ptr(out)),
@@ -393,12 +420,14 @@ def pdit_beta_schedule(kind: str, sweeps: int, beta_max: float) -> np.ndarray:
 
 
 def pdit_anneal_noalloc(n: int, D_ptr: int, F_ptr: int, replicas: int, beta_ptr: int, sweeps: int,
-                        seed: int, best_perm_ptr: int, best_cost_ptr: int, stream_ptr: int = 0) -> int:
-    """The allocation-free entry point on raw device pointers; returns the code."""
+                        seed: int, best_perm_ptr: int, best_cost_ptr: int, status_ptr: int = 0,
+                        stream_ptr: int = 0) -> int:
+    """The allocation-free entry point on raw device pointers (status_ptr 0:
+    the audit bits are not reported); returns the code."""
     return lib().pdit_anneal_noalloc(n, ctypes.c_void_p(D_ptr), ctypes.c_void_p(F_ptr), replicas,
                                      ctypes.c_void_p(beta_ptr), sweeps, seed & 0xFFFFFFFFFFFFFFFF,
                                      ctypes.c_void_p(best_perm_ptr), ctypes.c_void_p(best_cost_ptr),
-                                     ctypes.c_void_p(stream_ptr))
+                                     ctypes.c_void_p(status_ptr), ctypes.c_void_p(stream_ptr))
 
 
 def opts(**kw) -> pdit_opts:
@@ -457,16 +486,17 @@ def anneal_device(q: Qap, replicas: int, beta, sweeps: int, seed: int, *, mode: 
              exchange_period=exchange_period, timeout_periods=timeout_periods,
              sweep_begin=sweep_begin, sweep_end=sweep_end,
              flags=PDIT_FLAG_RESUME if resume else 0, stream=st.cuda_stream)
-    if workspace is None:
-        need = pdit_workspace_bytes(q, o)
-        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
-    o.workspace = workspace.data_ptr()
-    o.workspace_bytes = workspace.numel()
     for k, t in out.items():
         setattr(o, k, t.data_ptr())
     if target is not None:
         o.target = target.data_ptr()
         o.stop_at_target = 1 if stop_at_target else 0
+    if workspace is None:
+        # sized for these exact options (the outputs asked for can change the plan)
+        need = pdit_workspace_bytes(q, o)
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    o.workspace = workspace.data_ptr()
+    o.workspace_bytes = workspace.numel()
     pdit_anneal_ex(q, o)
     out["workspace"] = workspace
     return out

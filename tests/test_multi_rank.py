@@ -110,3 +110,44 @@ def test_ties_across_ranks_go_to_the_lowest_global_replica():
         assert cost == 42
         assert gid == 5  # rank 0's replica 5 (global 5) beats rank 1's replica 4 (global 12)
         assert perm == list(np.arange(6)[::-1])
+
+
+def _report_main(rank, world, port, out_q):
+    import torch.distributed as dist
+
+    from paper_2605_24408_gb300 import multi
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        base, cnt = multi.shard(rank, world, 4)
+        # per-replica best costs of each rank's shard, as the sharded benchmark
+        # reads them back: rank 0's best is 7 (local 1 and 2 tie), rank 1's is 6
+        # (local 2 and 3 tie), so the answer is global replica 4 + 2 = 6
+        rep_best = [[9, 7, 7, 8], [9, 9, 6, 6]][rank]
+        perm = np.arange(5, dtype=np.int32) + 10 * rank
+        assert multi.rank_winner(rep_best) == [1, 2][rank]
+        cost, gid, p = multi.rank_result(rep_best, perm, base)
+        out_q.put((rank, cost, gid, p.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_report_names_the_winning_global_replica():
+    """The sharded benchmark's final answer: the winning replica's global id,
+    not the rank's first replica, and that rank's permutation."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_report_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, cost, gid, perm in results:
+        assert (cost, gid) == (6, 6)
+        assert perm == list(np.arange(5) + 10)
