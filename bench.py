@@ -63,11 +63,12 @@ WORKLOAD_TEXT = {
 METRIC = "p-dit updates/s"
 L2_FLUSH_BYTES = 512 << 20
 SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM per clock (32 banks x 4 B)
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_kernel_n100_traffic.json")
-# the sweep kernel's own sources; the stored DRAM counters also record the
-# launch shape they were taken with, and both must match to be reported
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dot_kernel_n100_traffic.json")
+# the n100 kernel's own sources; the stored DRAM counters also record the
+# kernel and the launch shape they were taken with, and all must match to be
+# reported
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_24408_gb300", "csrc", f)
-                  for f in ("pdit_sweep.cuh", "pdit_sweep_i8.cu")]
+                  for f in ("pdit_sweep.cuh", "pdit_dot.cu")]
 
 
 def kernel_source_sha() -> str:
@@ -126,6 +127,31 @@ def algorithmic_bytes_per_update(n: int, dt_bytes: int, accept_frac: float, pend
             gather += 2 * n * dt_bytes
             swap += 8 * n * n / pending + 4 * n * dt_bytes + 4 * n
     return gather + accept_frac * swap
+
+
+def product_stride(n: int) -> int:
+    """Row stride in bytes of D and of the permuted flow matrix in the
+    dot-product kernel: 16 bytes x the smallest odd number >= n / 16."""
+    s16 = (n + 15) // 16
+    return 16 * (s16 + 1 - s16 % 2)
+
+
+def product_bytes_per_update(n: int, accept_frac: float) -> float:
+    """Shared-memory bytes one update moves in the dot-product kernel
+    (row stride S): for every candidate its row of D and its row of the
+    permuted flow matrix Q (2 N S), the updating location's two rows (2 S),
+    D[i][j] and Q[i][j] (2 N) and h[i] (4); per accepted swap the p-diagonal
+    update reads two D rows and two Q rows (4 N) and writes h (4 N), the two
+    Q rows are exchanged (4 S: read and written) and so are two columns
+    (4 N), and p moves (16)."""
+    S = product_stride(n)
+    return 2 * n * S + 2 * S + 2 * n + 4 + accept_frac * (12 * n + 4 * S + 16)
+
+
+def product_dp4a_per_update(n: int) -> int:
+    """dp4a operations per update of the dot-product kernel: two dot
+    products of S / 4 words for each of the N candidates."""
+    return 2 * n * (product_stride(n) // 4)
 
 
 def class_bytes_per_update(n: int, dt_bytes: int, accept_frac: float) -> float:
@@ -591,6 +617,11 @@ def main():
     for k, t in outs.items():
         setattr(o, k, t.data_ptr())
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # on-chip peaks of this GPU (a few milliseconds, before the timed region)
+    try:
+        peaks = P.pdit_probe_peaks(4000)
+    except P.PditError:
+        peaks = None
 
     def step():
         P.pdit_anneal_ex(q, o)
@@ -698,23 +729,46 @@ def main():
     kname = "sweep_kernel<int8,%d,%d,%s,%d>" % (shape["candidates_per_thread"], shape["warps_per_replica"],
                                                 "smem" if shape["tables_in_smem"] else "global",
                                                 shape["pending_swaps"])
+    products = shape.get("influence") == "products" and not class_path
+    alu = None
+    kernel_s = tot_ms / 1000.0 / args.steps
     if class_path:
         # the flow-class kernel keeps no table: its own traffic is the figure
         bpu = bpu_design = class_bytes_per_update(n, dt_bytes, accept_frac)
         basis = ("(17 + dt) N + A (2 N dt + 8 N): the flow-class kernel's gathers plus, per accepted "
                  "swap, at most two D rows and the G vector (A counts swaps within a class too)")
         kname = "class_kernel<int8,%d,%d>" % (shape["candidates_per_thread"], shape["warps_per_replica"])
-    kernel_s = tot_ms / 1000.0 / args.steps
+    elif products:
+        # no table: the kernel's own traffic is the design figure; the
+        # method's figure stays the basis of `achieved`
+        bpu_design = product_bytes_per_update(n, accept_frac)
+        kname = "dot_kernel<%d,%d>" % (shape["candidates_per_thread"], shape["warps_per_replica"])
+        dp4a = product_dp4a_per_update(n)
+        alu = {"op": "dp4a", "per_update": dp4a, "achieved_ops_per_s": dp4a * upd_rank / kernel_s}
     achieved = bpu * upd_rank / kernel_s / 1e9
     sm_mhz = clk.get("sm_mhz") or 0.0
-    peak = props.multi_processor_count * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9 if sm_mhz else None
+    sms = props.multi_processor_count
+    if peaks and sm_mhz:
+        peak = sms * peaks["smem_bytes_per_clk_sm"] * sm_mhz * 1e6 / 1e9
+        peak_source = ("measured: pdit_probe_peaks %.1f B/clk/SM (conflict-free 128-bit ld.shared) x %d SMs x "
+                       "median SM clock under load (%s MHz)" % (peaks["smem_bytes_per_clk_sm"], sms, sm_mhz))
+        if alu is not None:
+            alu["peak_ops_per_s"] = sms * peaks["dp4a_ops_per_clk_sm"] * sm_mhz * 1e6
+            alu["frac"] = alu["achieved_ops_per_s"] / alu["peak_ops_per_s"]
+            alu["peak_source"] = "measured: pdit_probe_peaks %.1f dp4a/clk/SM x %d SMs x %s MHz" % (
+                peaks["dp4a_ops_per_clk_sm"], sms, sm_mhz)
+    else:
+        peak = sms * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9 if sm_mhz else None
+        peak_source = "derived: %d SMs x %d B/clk x median SM clock under load (%s MHz)" % (
+            sms, SMEM_BYTES_PER_CLK, sm_mhz)
     traffic = None
     try:
         # the stored DRAM counters describe the default workload's kernel only
         if args.workload == "n100" and args.mode == "anneal" and not (args.wpr or args.pk or args.rpc or args.place):
             with open(TRAFFIC_FILE) as fh:
                 tr = json.load(fh)
-            if tr.get("source_sha") == kernel_source_sha() and tr.get("launch") == shape:
+            if tr.get("kernel") == kname and tr.get("source_sha") == kernel_source_sha() and \
+                    tr.get("launch") == shape:
                 traffic = tr.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -727,7 +781,7 @@ def main():
                                              WORKLOAD_TEXT[args.workload])
                    if args.workload in WORKLOAD_TEXT else args.workload,
                    "mode": args.mode,
-                   "update": "flow classes" if class_path else "table",
+                   "update": "flow classes" if class_path else ("dot products" if products else "table"),
                    "replicas_per_gpu": replicas, "sweeps": sweeps, "schedule": "pt ladder" if pt else kind, "seed": 0,
                    "global_batch": replicas * world, "seq_len": n,
                    "parallelism": "replicas sharded over %d GPU(s)" % world,
@@ -750,8 +804,7 @@ def main():
                      "bytes_per_update_basis": basis,
                      "design_bytes_per_update": bpu_design,
                      "design_frac": (bpu_design * upd_rank / kernel_s / 1e9 / peak) if peak else None,
-                     "peak_source": "derived: %d SMs x %d B/clk x median SM clock under load (%s MHz)"
-                                    % (props.multi_processor_count, SMEM_BYTES_PER_CLK, sm_mhz)},
+                     "peak_source": peak_source, "alu": alu},
         "wall_s_timed_region": wall,
     }
     if pt:

@@ -174,11 +174,12 @@ int pdit_launch_shape(const pdit_qap *h, int replicas, int *shape);
  *                             next call). Two-level-flow instances keep the
  *                             flow-class kernel unless pdit_set_class_update
  *                             turns it off.
- *   PDIT_INFLUENCE_AUTO     : products where eligible, unless a table knob
- *                             (pending swaps, placement) is set; the table
- *                             otherwise (also for the concurrent-update mode,
- *                             for calls that dump the tables, and for sizes
- *                             with no compiled product shape).
+ *   PDIT_INFLUENCE_AUTO     : products where eligible and where shared
+ *                             memory holds at least 3 replicas per SM (N up
+ *                             to about 200), unless a table knob (pending
+ *                             swaps, placement) is set; the table otherwise
+ *                             (also for the concurrent-update mode and for
+ *                             calls that dump the tables).
  * The entries are the same exact integers either way, so results do not
  * depend on the choice. Errors: PDIT_EINVAL.
  */
@@ -462,18 +463,22 @@ void pdit_batch_destroy(pdit_batch *b);
  * thread, admits queued requests in arrival order while active slots and the
  * device-memory budget allow (each request's footprint: its matrices,
  * replica state and schedule), runs the next `slice_sweeps` sweeps of every
- * active request in one batched launch per kernel shape (replica state stays
- * on the device between slices; a slice resumes exactly where the previous
- * one stopped), and retires the requests whose schedule has ended. A
- * request's result is the same as a single pdit_anneal_ex call with
- * instance_id = its request id: alone or in any mix.
+ * active request in one batched launch per kernel shape, and retires the
+ * requests whose schedule has ended. Every replica's whole state stays on
+ * the device between slices (permutation, energies, best-so-far, and the
+ * influence table of the table kernels or the permuted flow matrix of the
+ * dot-product kernel), so a slice resumes exactly where the previous one
+ * stopped without rebuilding anything. A request's result is the same as a
+ * single pdit_anneal_ex call with instance_id = its request id: alone or in
+ * any mix. Device memory of requests is allocated and released in stream
+ * order (cudaMallocAsync / cudaFreeAsync on the device's default pool).
  */
 typedef struct pdit_server pdit_server;
 
 /*
  * pdit_server_create -- device_budget_bytes: device memory the admitted
  * requests may hold together (one oversize request is still admitted when
- * nothing else is active); slice_sweeps: sweeps per tick (>= 1);
+ * nothing else holds memory); slice_sweeps: sweeps per tick (>= 1);
  * max_active: requests resident at once. Errors: PDIT_EINVAL, PDIT_ECUDA.
  */
 int pdit_server_create(size_t device_budget_bytes, int slice_sweeps, int max_active, pdit_server **out);
@@ -491,9 +496,14 @@ int pdit_server_submit(pdit_server *s, int n, const int32_t *D, const int32_t *F
                        uint64_t seed, uint32_t request_id, const float *beta, int64_t *ticket);
 
 /*
- * pdit_server_tick -- one scheduling step (admit, one slice for every
- * active request, retire). Synchronous on the server's own stream.
- * Reports how many requests are active and queued afterwards.
+ * pdit_server_tick -- one scheduling step: pick up the results of earlier
+ * slices that have completed, admit, and enqueue one slice for every active
+ * request on the server's streams. Asynchronous: the host prepares the next
+ * tick while the GPU runs this one (two ticks in flight at most; the call
+ * waits only for the tick before the previous one, or, when nothing is left
+ * to enqueue, for the oldest outstanding tick). A request counts as active
+ * until its result has been picked up. Reports how many requests are active
+ * and queued afterwards.
  * Errors: PDIT_EINVAL, PDIT_ECUDA, PDIT_ENOTSUP.
  */
 int pdit_server_tick(pdit_server *s, int *active, int *queued);
@@ -501,7 +511,8 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued);
 /*
  * pdit_server_result -- state of a request (0 queued, 1 running, 2 done,
  * 3 failed at admission); when done, its best permutation (host [n]), best
- * cost and latency (seconds from submit to the end of its last slice).
+ * cost and latency (seconds from submit to the tick that picked up its
+ * result, after its last slice completed).
  * Thread-safe. Errors: PDIT_EINVAL.
  */
 int pdit_server_result(pdit_server *s, int64_t ticket, int *state, int32_t *best_perm, int64_t *best_cost,
@@ -552,12 +563,14 @@ int pdit_write_qaplib_solution(const char *path, int n, int64_t cost, const int3
  * reports none): one CTA of 1024 threads per SM, timed with CUDA events and
  * with SM cycles (clock64).
  *   iters : loop trips of each probe (>= 1; 2000 takes a few milliseconds).
- *   out   : host array of 6 doubles:
+ *   out   : host array of 10 doubles:
  *           [0] shared-memory load bandwidth, bytes/s over all SMs
  *               (conflict-free 128-bit ld.shared, 512 contiguous bytes per warp);
  *           [1] the same in bytes per SM clock per SM;
  *           [2] dp4a.s32.s32 thread-operations/s over all SMs;  [3] per SM clock per SM;
- *           [4] mad.lo.s32 thread-operations/s over all SMs;    [5] per SM clock per SM.
+ *           [4] mad.lo.s32 thread-operations/s over all SMs;    [5] per SM clock per SM;
+ *           [6] mma.sync m16n8k16 f16 -> f32 multiply-adds/s;    [7] per SM clock per SM;
+ *           [8] mma.sync m16n8k32 s8 -> s32 multiply-adds/s;     [9] per SM clock per SM.
  * Synchronous on a private stream; allocates and frees two small device
  * buffers. Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ECUDA.
  */

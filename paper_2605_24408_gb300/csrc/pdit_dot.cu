@@ -37,6 +37,15 @@ __device__ __forceinline__ void dot4(const int4 x, const int4 y, int &acc) {
     acc = __dp4a(x.w, y.w, acc);
 }
 
+// 128-bit load from a 32-bit shared-window address. Volatile, so it stays on
+// its side of the group barriers (the rows it reads are rewritten between
+// them).
+__device__ __forceinline__ int4 lds128(uint32_t addr) {
+    int4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+
 // Location held by slot `row` (inverse of the slot map).
 template <int MAXK>
 __device__ __forceinline__ int dot_loc(int row, int ta) {
@@ -72,7 +81,14 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
     }
     group_sync<WPR>(bar);
 
-    // ---- Q[slot(x)][y] = F[p(x)][p(y)], zero outside n x n
+    // ---- Q[slot(x)][y] = F[p(x)][p(y)], zero outside n x n; or the copy
+    // saved by the previous call on this replica (a.tables, rows x stride
+    // bytes per replica)
+    const size_t qbytes = (size_t)rows * S8;
+    if (a.table_in) {
+        const int4 *src = reinterpret_cast<const int4 *>(reinterpret_cast<const int8_t *>(a.tables) + (size_t)r * qbytes);
+        for (int idx = t; idx < (int)(qbytes / 16); idx += G) reinterpret_cast<int4 *>(sQ)[idx] = src[idx];
+    } else
     for (int idx = t; idx < rows * W4; idx += G) {
         const int row = idx / W4, w = idx - row * W4;
         const int x = dot_loc<MAXK>(row, TA);
@@ -139,6 +155,15 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
     const float beta_fixed = a.sweep_end <= a.sweep_begin ? 0.0f
                            : a.mode == 1 ? a.beta[a.rung[r]] : a.mode == 2 ? a.beta[r] : 0.0f;
     const int zero_diag = a.zero_diag;
+    // shared-window addresses of the rows of this thread's locations
+    const uint32_t sD32 = (uint32_t)__cvta_generic_to_shared(sD);
+    const uint32_t sQ32 = (uint32_t)__cvta_generic_to_shared(sQ);
+    uint32_t rowD[MAXK], rowQ[MAXK];
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k) {
+        rowD[k] = sD32 + (uint32_t)((k * TA + t) * S8);
+        rowQ[k] = sQ32 + (uint32_t)((k * TA + t) * S8);
+    }
 
     for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
         if (a.stop) {
@@ -169,15 +194,15 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
 #pragma unroll
                 for (int k = 0; k < MAXK; ++k) rowv[k] = colv[k] = 0;
                 if (active) {
+                    const uint32_t aDi = sD32 + (uint32_t)(si * S8), aQi = sQ32 + (uint32_t)(si * S8);
 #pragma unroll 1
                     for (int c = 0; c < S8; c += 16) {  // one 16-byte chunk of every row at a time
-                        const int4 di = *reinterpret_cast<const int4 *>(Di + c);
-                        const int4 qi = *reinterpret_cast<const int4 *>(Qi + c);
+                        const int4 di = lds128(aDi + c);
+                        const int4 qi = lds128(aQi + c);
 #pragma unroll
                         for (int k = 0; k < MAXK; ++k) {
-                            const size_t off = (size_t)(k * TA + t) * S8 + c;
-                            dot4(di, *reinterpret_cast<const int4 *>(sQ + off), rowv[k]);
-                            dot4(*reinterpret_cast<const int4 *>(sD + off), qi, colv[k]);
+                            dot4(di, lds128(rowQ[k] + c), rowv[k]);
+                            dot4(lds128(rowD[k] + c), qi, colv[k]);
                         }
                     }
                 }
@@ -326,7 +351,33 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
         a.best_sweep[r] = bsweep;
         a.accepted[r] = acc_moves;
     }
+    if (a.table_out) {
+        int4 *dst = reinterpret_cast<int4 *>(reinterpret_cast<int8_t *>(a.tables) + (size_t)r * qbytes);
+        for (int idx = t; idx < (int)(qbytes / 16); idx += G) dst[idx] = reinterpret_cast<const int4 *>(sQ)[idx];
+    }
     group_sync<WPR>(bar);
+}
+
+// D of an n-location instance as int8 rows in slot order (rows x stride
+// bytes), zero outside n x n.
+template <int MAXK>
+__device__ __forceinline__ void stage_dot_d(const int32_t *D, int n, int S8, int8_t *sD) {
+    const int W4 = S8 >> 2;
+    const int TA = (n + MAXK - 1) / MAXK;
+    const int rows = TA * MAXK;
+    for (int idx = threadIdx.x; idx < rows * W4; idx += blockDim.x) {
+        const int row = idx / W4, w = idx - row * W4;
+        const int x = dot_loc<MAXK>(row, TA);
+        uint32_t word = 0;
+        if (x < n) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int y = 4 * w + b;
+                if (y < n) word |= (uint32_t)(uint8_t)(int8_t)D[(size_t)x * n + y] << (8 * b);
+            }
+        }
+        reinterpret_cast<uint32_t *>(sD + (size_t)row * S8)[w] = word;
+    }
 }
 
 // Persistent: each group of 32 * WPR threads pulls replicas from a.queue.
@@ -338,7 +389,6 @@ __global__ void __launch_bounds__(dot_bound(MAXK, WPR)) dot_kernel(const SweepAr
     constexpr int G = 32 * WPR;
     const int n = a.n;
     const int S8 = a.stride;
-    const int W4 = S8 >> 2;
     const int TA = (n + MAXK - 1) / MAXK;
     const int rows = TA * MAXK;
     const int npad = (n + 3) & ~3;
@@ -346,19 +396,7 @@ __global__ void __launch_bounds__(dot_bound(MAXK, WPR)) dot_kernel(const SweepAr
     const int t = threadIdx.x % G;
     const int bar = 1 + grp;  // named barrier of this group (WPR > 1); 0 is __syncthreads
     int8_t *sD = reinterpret_cast<int8_t *>(smem);
-    for (int idx = threadIdx.x; idx < rows * W4; idx += blockDim.x) {
-        const int row = idx / W4, w = idx - row * W4;
-        const int x = dot_loc<MAXK>(row, TA);
-        uint32_t word = 0;
-        if (x < n) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int y = 4 * w + b;
-                if (y < n) word |= (uint32_t)(uint8_t)(int8_t)a.D[(size_t)x * n + y] << (8 * b);
-            }
-        }
-        reinterpret_cast<uint32_t *>(sD + (size_t)row * S8)[w] = word;
-    }
+    stage_dot_d<MAXK>(a.D, n, S8, sD);
     __syncthreads();
     unsigned char *gb = smem + a.df_bytes + (size_t)grp * a.group_bytes;
     GroupScratch *gs = reinterpret_cast<GroupScratch *>(gb);
@@ -371,6 +409,52 @@ __global__ void __launch_bounds__(dot_bound(MAXK, WPR)) dot_kernel(const SweepAr
         const int item = gs->item;
         if (item >= a.replicas) break;
         run_dot_replica<MAXK, WPR>(a, item, t, bar, sD, sQ, sp, sh, gs);
+    }
+}
+
+// Persistent multi-instance kernel: CTAs take (instance, block of replicas)
+// units from `queue` and restage D when they move to another instance.
+// Every instance of a launch shares the compiled shape (MAXK, WPR).
+template <int MAXK, int WPR>
+__global__ void __launch_bounds__(dot_bound(MAXK, WPR))
+    dot_batch_kernel(const SweepArgs *__restrict__ descs, const BatchUnit *__restrict__ units, int nunits,
+                     int *queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SweepArgs sa;
+    __shared__ int s_unit;
+    constexpr int G = 32 * WPR;
+    const int grp = threadIdx.x / G;
+    const int t = threadIdx.x % G;
+    const int bar = 1 + grp;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(queue, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= nunits) break;
+        const BatchUnit bu = units[u];
+        if (bu.inst != cur) {
+            // descriptor and D of the new instance
+            const int *src = reinterpret_cast<const int *>(descs + bu.inst);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+            stage_dot_d<MAXK>(descs[bu.inst].D, descs[bu.inst].n, descs[bu.inst].stride,
+                              reinterpret_cast<int8_t *>(smem));
+            cur = bu.inst;
+        }
+        __syncthreads();
+        const int n = sa.n;
+        const int r = bu.r0 + grp;
+        if (grp < sa.groups && r < sa.replicas) {
+            const int rows = ((n + MAXK - 1) / MAXK) * MAXK;
+            const int npad = (n + 3) & ~3;
+            unsigned char *gb = smem + sa.df_bytes + (size_t)grp * sa.group_bytes;
+            GroupScratch *gs = reinterpret_cast<GroupScratch *>(gb);
+            int8_t *sQ = reinterpret_cast<int8_t *>(gb + kScratchBytes);
+            int32_t *sp = reinterpret_cast<int32_t *>(gb + kScratchBytes + (size_t)rows * sa.stride);
+            int32_t *sh = sp + npad;
+            run_dot_replica<MAXK, WPR>(sa, r, t, bar, reinterpret_cast<const int8_t *>(smem), sQ, sp, sh, gs);
+        }
     }
 }
 
@@ -403,6 +487,36 @@ bool dot_shape_compiled(int maxk, int wpr) {
     PDIT_DOT_SHAPES(PDIT_DOT_HAS)
 #undef PDIT_DOT_HAS
     return false;
+}
+
+template <int MAXK, int WPR>
+static int dot_batch_one(const SweepArgs *d, const BatchUnit *u, int nu, int *q, int grid, int threads,
+                         size_t smem, cudaStream_t st, int *blocks, bool query) {
+    auto fn = dot_batch_kernel<MAXK, WPR>;
+    if (threads > dot_bound(MAXK, WPR)) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    if (query) return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem);
+    fn<<<grid, threads, smem, st>>>(d, u, nu, q);
+    return (int)cudaGetLastError();
+}
+
+static int dot_batch_dispatch(int maxk, int wpr, const SweepArgs *d, const BatchUnit *u, int nu, int *q, int grid,
+                              int threads, size_t smem, cudaStream_t st, int *blocks, bool query) {
+#define PDIT_DOT_BATCH_CASE(MK, W) \
+    if (maxk == MK && wpr == W) return dot_batch_one<MK, W>(d, u, nu, q, grid, threads, smem, st, blocks, query);
+    PDIT_DOT_SHAPES(PDIT_DOT_BATCH_CASE)
+#undef PDIT_DOT_BATCH_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+int dot_batch_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks) {
+    return dot_batch_dispatch(maxk, wpr, nullptr, nullptr, 0, nullptr, 0, threads, smem, nullptr, blocks, true);
+}
+
+int dot_batch_launch(int maxk, int wpr, const SweepArgs *descs, const BatchUnit *units, int nunits, int *queue,
+                     int grid, int threads, size_t smem, cudaStream_t stream) {
+    return dot_batch_dispatch(maxk, wpr, descs, units, nunits, queue, grid, threads, smem, stream, nullptr, false);
 }
 
 int dot_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks) {

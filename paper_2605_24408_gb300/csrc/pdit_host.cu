@@ -30,6 +30,7 @@ struct pdit_qap {
     uint8_t *dx = nullptr;  // x_c on the device
     int packed_ok = 0;      // max-min of D and of F <= 127: swap factors fit int8
     std::vector<int32_t> hD, hF;
+    std::vector<uint8_t> cls_x;  // class bit of every facility (two-level flows)
     int32_t *dD = nullptr, *dF = nullptr;
     // owned by the handle, grown on demand
     void *ws = nullptr;
@@ -292,7 +293,7 @@ int class_launch(int dt, const Plan &p, const pdit::SweepArgs &a, cudaStream_t s
 // Launch shape of the dot-product kernel (pdit_dot.cu): D as int8 in slot
 // order once per CTA, then per replica group: scratch, the permuted flow
 // matrix Q (rows x stride bytes), p and h. Row stride: 16 bytes x odd.
-int make_dot_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
+int make_dot_plan(const pdit_qap *h, int replicas, int wpr, Plan *p, size_t reserve = 0) {
     const int n = h->n;
     const int cover = cover_for(n);
     const int npad = (n + 3) & ~3;
@@ -303,9 +304,8 @@ int make_dot_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
     p->pk = 1;
     p->stride = 16 * s16;
     p->dstride = n;
-    p->table_elems = 0;
     p->sv_len = 0;
-    const size_t budget = h->smem_optin;
+    const size_t budget = h->smem_optin - reserve;
     auto sizes = [&](int maxk, size_t *df, size_t *grp) {
         const size_t rows = (size_t)((n + maxk - 1) / maxk) * maxk;
         *df = rows * p->stride;
@@ -341,6 +341,8 @@ int make_dot_plan(const pdit_qap *h, int replicas, int wpr, Plan *p) {
     p->maxk = cover / (32 * wpr);
     if (!pdit::dot_shape_compiled(p->maxk, wpr)) return PDIT_ENOTSUP;
     sizes(p->maxk, &p->df_bytes, &p->group_bytes);
+    // int32 words of one replica's saved permuted flow matrix (rows x stride bytes)
+    p->table_elems = (size_t)((n + p->maxk - 1) / p->maxk) * p->maxk * p->stride / 4;
     if (p->df_bytes + p->group_bytes > budget) return PDIT_ENOTSUP;
     const int fit = (int)((budget - p->df_bytes) / p->group_bytes);
     int g = std::min(fit, pdit::dot_bound(p->maxk, wpr) / (32 * wpr));
@@ -371,6 +373,19 @@ bool use_class_path(const pdit_qap *h, const pdit_opts *o) {
     return h->cls && h->use_cls && o->mode != PDIT_MODE_CUPIM && !o->tables;
 }
 
+// The automatic choice of the dot kernel: it keeps an N x N byte matrix per
+// replica, and where shared memory holds fewer than 3 replicas per SM (N
+// above about 200) the table kernels are faster (measured: N = 190 2.38e8
+// against 1.94e8 updates/s, N = 256 1.30e8 against 1.84e8). PDIT_ENOTSUP
+// when it does not take the dot kernel.
+int auto_dot_plan(const pdit_qap *h, int replicas, Plan *p, size_t reserve) {
+    Plan full;
+    int rc = make_dot_plan(h, 1 << 28, h->force_wpr, &full, reserve);
+    if (rc != PDIT_OK) return rc;
+    if (full.groups * std::max(1, full.grid / std::max(1, h->num_sms)) < 3) return PDIT_ENOTSUP;
+    return make_dot_plan(h, replicas, h->force_wpr, p, reserve);
+}
+
 // Whether a call runs the dot-product kernel: an eligible instance in a
 // sequential mode, without a request for the table dump or for table-kernel
 // knobs (pending terms, table placement), unless the handle asks for it.
@@ -388,11 +403,32 @@ int plan_for(const pdit_qap *h, const pdit_opts *o, Plan *p) {
         return make_dot_plan(h, o->replicas, h->force_wpr, p);
     }
     if (use_dot_path(h, o)) {
-        const int rc = make_dot_plan(h, o->replicas, h->force_wpr, p);
+        const int rc = auto_dot_plan(h, o->replicas, p, 0);
         if (rc != PDIT_ENOTSUP) return rc;
-        *p = Plan();  // no dot shape for this size or mapping: the table kernels
+        *p = Plan();  // no suitable dot shape: the table kernels
     }
     return make_plan(h, o->replicas, h->force_wpr, h->force_pk, p, 0, o->mode == PDIT_MODE_CUPIM);
+}
+
+// Plan of one instance in a multi-instance launch (batches, the server):
+// the dot kernel where the automatic rule takes it, else the table kernels;
+// the kernels keep their descriptor in `reserve` bytes of static shared
+// memory.
+int batch_plan(const pdit_qap *h, Plan *p, size_t reserve) {
+    if (!h->cls || !h->use_cls) {
+        if (h->force_infl == PDIT_INFLUENCE_PRODUCTS) {
+            if (!dot_eligible(h)) return PDIT_ENOTSUP;
+            return make_dot_plan(h, 1 << 28, h->force_wpr, p, reserve);
+        }
+        pdit_opts o;
+        pdit_opts_init(&o);
+        if (use_dot_path(h, &o)) {
+            const int rc = auto_dot_plan(h, 1 << 28, p, reserve);
+            if (rc != PDIT_ENOTSUP) return rc;
+            *p = Plan();
+        }
+    }
+    return make_plan(h, 1 << 28, h->force_wpr, h->force_pk, p, reserve);
 }
 
 struct Workspace {
@@ -401,9 +437,14 @@ struct Workspace {
     size_t bytes;
 };
 
-bool needs_tables(const pdit_opts *o, const Plan &p) { return !p.dot && (o->mode == PDIT_MODE_PT || !p.tsmem); }
+// Whether the workspace holds every replica's table (the table kernels: PT
+// segments and tables in global memory; `persist`: any kernel whose state is
+// kept between calls by the server, the dot kernel's permuted flow matrix).
+bool needs_tables(const pdit_opts *o, const Plan &p, bool persist = false) {
+    return persist || (!p.dot && (o->mode == PDIT_MODE_PT || !p.tsmem));
+}
 
-Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base) {
+Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base, bool persist = false) {
     const size_t R = (size_t)o->replicas, n = (size_t)h->n;
     size_t off = 0;
     Workspace w{};
@@ -424,7 +465,7 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.queue = (int32_t *)take(4 * 64);
     w.status = (int32_t *)take(4);
     w.done = (int32_t *)take(4);
-    w.tables = needs_tables(o, p) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
+    w.tables = needs_tables(o, p, persist) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
     w.bytes = off;
     return w;
 }
@@ -646,7 +687,11 @@ void pdit_opts_init(pdit_opts *o) {
     o->timeout_periods = 100;
 }
 
-int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
+}  // extern "C"
+
+// Host side of qap_create: validation, the instance form, the staging
+// width and the device attributes; no device memory yet.
+int qap_prepare(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     if (!out) return PDIT_EINVAL;
     *out = nullptr;
     if (n < 2 || n > PDIT_N_MAX || !D || !F) return PDIT_EINVAL;
@@ -695,14 +740,32 @@ int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
     h->smem_optin = (size_t)v;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, h->device);
     h->l2_bytes = (size_t)v;
+    if (e != cudaSuccess) {
+        const int rc = cuda_fail(e, "qap_create");
+        delete h;
+        return rc;
+    }
+    h->cls_x.assign(cx.begin(), cx.end());
+    *out = h;
+    return PDIT_OK;
+}
+
+extern "C" {
+
+int qap_create(int n, const int32_t *D, const int32_t *F, pdit_qap **out) {
+    int rc = qap_prepare(n, D, F, out);
+    if (rc) return rc;
+    pdit_qap *h = *out;
+    *out = nullptr;
     const size_t bytes = sizeof(int32_t) * (size_t)n * n;
+    cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dD, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->dF, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(h->dD, D, bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->dF, F, bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && h->cls) {
         e = cudaMalloc((void **)&h->dx, (size_t)n);
-        if (e == cudaSuccess) e = cudaMemcpy(h->dx, cx.data(), (size_t)n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->dx, h->cls_x.data(), (size_t)n, cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
         const int rc = (e == cudaErrorMemoryAllocation) ? PDIT_ENOMEM : cuda_fail(e, "qap_create");
@@ -1327,7 +1390,7 @@ struct BatchOut {
 
 struct BatchClass {
     int dt = 1, maxk = 1, wpr = 1, pk = 1;
-    bool tsmem = true, asym = false;
+    bool tsmem = true, asym = false, dot = false;
     int threads = 32, grid = 1, nunits = 0;
     size_t smem = 0;
     std::vector<int> items;
@@ -1344,6 +1407,7 @@ int batch_blocks_t(const BatchClass &c, int *blocks) {
 }
 
 int batch_blocks(const BatchClass &c, int *blocks) {
+    if (c.dot) return pdit::dot_batch_blocks_per_sm(c.maxk, c.wpr, c.threads, c.smem, blocks);
     return c.asym ? batch_blocks_t<true>(c, blocks) : batch_blocks_t<false>(c, blocks);
 }
 
@@ -1360,12 +1424,29 @@ int batch_launch_t(const BatchClass &c, const pdit::SweepArgs *descs, int *queue
 }
 
 int batch_launch(const BatchClass &c, const pdit::SweepArgs *descs, int *queue) {
+    if (c.dot)
+        return pdit::dot_batch_launch(c.maxk, c.wpr, descs, c.d_units, c.nunits, queue, c.grid, c.threads, c.smem,
+                                      c.stream);
     return c.asym ? batch_launch_t<true>(c, descs, queue) : batch_launch_t<false>(c, descs, queue);
 }
 
 // Same compiled kernel shape.
 bool same_class(const BatchClass &x, int dt, bool asym, const Plan &p) {
+    if (x.dot || p.dot) return x.dot == p.dot && x.maxk == p.maxk && x.wpr == p.wpr;
     return x.dt == dt && x.asym == asym && x.maxk == p.maxk && x.wpr == p.wpr && x.pk == p.pk && x.tsmem == p.tsmem;
+}
+
+// A new shape class for plan p.
+BatchClass class_for(int dt, bool asym, const Plan &p) {
+    BatchClass x;
+    x.dt = dt;
+    x.asym = asym;
+    x.dot = p.dot;
+    x.maxk = p.maxk;
+    x.wpr = p.wpr;
+    x.pk = p.pk;
+    x.tsmem = p.tsmem;
+    return x;
 }
 
 // Per instance: reset its time-to-target outputs and stop flag.
@@ -1503,8 +1584,8 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
     size_t ws_total = 0;
     for (int k = 0; k < count; ++k) {
         pdit_qap *h = items[k].qap;
-        // the multi-instance kernel keeps its instance descriptor in static shared memory
-        int rc = make_plan(h, 1 << 28, h->force_wpr, h->force_pk, &plans[k], kBatchStaticSmem);
+        // the multi-instance kernels keep their instance descriptor in static shared memory
+        int rc = batch_plan(h, &plans[k], kBatchStaticSmem);
         if (rc) {
             delete b;
             return rc;
@@ -1524,14 +1605,7 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
         for (size_t c = 0; c < b->classes.size(); ++c)
             if (same_class(b->classes[c], dt, asym, p)) found = (int)c;
         if (found < 0) {
-            BatchClass x;
-            x.dt = dt;
-            x.asym = asym;
-            x.maxk = p.maxk;
-            x.wpr = p.wpr;
-            x.pk = p.pk;
-            x.tsmem = p.tsmem;
-            b->classes.push_back(x);
+            b->classes.push_back(class_for(dt, asym, p));
             found = (int)b->classes.size() - 1;
         }
         BatchClass &x = b->classes[found];
@@ -1704,6 +1778,21 @@ struct ServerRequest {
 
 }  // namespace
 
+// Host-side staging of one tick. Two of them alternate, so that the host
+// fills one while the copies of the other may still be pending on the GPU;
+// a buffer is reused only after its event has completed.
+struct TickBuf {
+    pdit::SweepArgs *h_descs = nullptr;
+    BatchOut *h_outs = nullptr;
+    pdit::BatchUnit *h_units = nullptr;
+    int32_t *h_perm = nullptr;  // results of the requests finishing with this tick: PDIT_N_MAX each
+    int64_t *h_cost = nullptr;
+    size_t cap_desc = 0, cap_units = 0, cap_res = 0;
+    cudaEvent_t done = nullptr;  // recorded after the tick's result copies
+    bool pending = false;
+    std::vector<ServerRequest *> finishing;
+};
+
 struct pdit_server {
     int device = 0;
     size_t budget = 0, used = 0;
@@ -1712,49 +1801,70 @@ struct pdit_server {
     std::vector<ServerRequest *> all;   // by ticket
     std::vector<ServerRequest *> queue; // FIFO of queued tickets
     std::vector<ServerRequest *> active;
-    // per-tick device/host staging (grown on demand)
-    pdit::SweepArgs *d_descs = nullptr, *h_descs = nullptr;
-    BatchOut *d_outs = nullptr, *h_outs = nullptr;
-    pdit::BatchUnit *d_units = nullptr, *h_units = nullptr;
-    int *d_queues = nullptr;
+    // device arrays of a tick (stream-ordered on `main`, so one set serves
+    // both host buffers), grown on demand
+    pdit::SweepArgs *d_descs = nullptr;
+    BatchOut *d_outs = nullptr;
+    pdit::BatchUnit *d_units = nullptr;
     size_t cap_desc = 0, cap_units = 0;
+    int *d_queues = nullptr;
+    TickBuf buf[2];
+    int cur = 0;
     std::vector<BatchClass> classes;  // streams and events reused
     cudaStream_t main = nullptr;
+    cudaStream_t upload = nullptr;   // admissions: allocations and copies of new requests
+    cudaEvent_t uploaded = nullptr;  // recorded after the last admission's copies
+    bool new_uploads = false;
     cudaEvent_t fork = nullptr;
     int64_t completed = 0;
 };
 
 namespace {
 
+// Stream-ordered release of a request's device memory, after the work
+// queued on the main stream (which has joined every kernel that used it):
+// no device-wide synchronisation, so the host keeps ahead of the GPU.
 void release_request(pdit_server *s, ServerRequest *r) {
-    cudaFree(r->ws);
-    cudaFree(r->dbeta);
-    cudaFree(r->dperm);
-    cudaFree(r->dcost);
+    void *bufs[] = {r->ws, r->dbeta, r->dperm, r->dcost, r->qap ? r->qap->dD : nullptr,
+                    r->qap ? r->qap->dF : nullptr, r->qap ? r->qap->dx : nullptr};
+    for (void *ptr : bufs)
+        if (ptr) cudaFreeAsync(ptr, s->main);
     r->ws = nullptr;
     r->dbeta = nullptr;
     r->dperm = nullptr;
     r->dcost = nullptr;
-    qap_destroy(r->qap);
+    if (r->qap) {
+        r->qap->dD = nullptr;
+        r->qap->dF = nullptr;
+        r->qap->dx = nullptr;
+    }
+    qap_destroy(r->qap);  // host state only now
     r->qap = nullptr;
     s->used -= std::min(s->used, r->footprint);
 }
 
-// Device memory a request holds while admitted.
+// Device memory a request holds while admitted: its workspace with every
+// replica's state kept between slices (the table of the table kernels, the
+// permuted flow matrix of the dot kernel), the matrices, the schedule and
+// the result.
 size_t request_footprint(const ServerRequest &r, const Plan &p) {
     pdit_opts o;
     pdit_opts_init(&o);
     o.replicas = r.replicas;
-    return carve(r.qap, &o, p, nullptr).bytes + (size_t)8 * r.n * r.n + 4 * (size_t)r.sweeps + 4 * r.n + 8 + 1024;
+    return carve(r.qap, &o, p, nullptr, true).bytes + (size_t)8 * r.n * r.n + 4 * (size_t)r.sweeps + 4 * r.n + 8 +
+           1024;
 }
 
 int admit(pdit_server *s, ServerRequest *r) {
-    int rc = qap_create(r->n, r->D.data(), r->F.data(), &r->qap);
+    int rc = qap_prepare(r->n, r->D.data(), r->F.data(), &r->qap);
     if (rc) return rc;
-    rc = make_plan(r->qap, 1 << 28, 0, 0, &r->plan, kBatchStaticSmem);
+    rc = batch_plan(r->qap, &r->plan, kBatchStaticSmem);
     if (rc) return rc;
     const size_t fp = request_footprint(*r, r->plan);
-    if (s->used + fp > s->budget && !s->active.empty()) return 1;  // wait for memory
+    // wait for memory; a request larger than the budget is admitted alone,
+    // once nothing else holds device memory (finished requests release
+    // theirs when their last tick has completed)
+    if (s->used + fp > s->budget && s->used > 0) return 1;
     if (r->beta.empty()) {
         double bmax = 0.0;
         pdit_beta_max(r->qap, &bmax);
@@ -1764,15 +1874,30 @@ int admit(pdit_server *s, ServerRequest *r) {
     pdit_opts o;
     pdit_opts_init(&o);
     o.replicas = r->replicas;
-    const size_t wsb = carve(r->qap, &o, r->plan, nullptr).bytes;
-    cudaError_t e = cudaMalloc(&r->ws, wsb);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&r->dbeta, sizeof(float) * std::max(r->sweeps, 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&r->dperm, sizeof(int32_t) * r->n);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&r->dcost, sizeof(int64_t));
+    const size_t wsb = carve(r->qap, &o, r->plan, nullptr, true).bytes;
+    // stream-ordered allocations and copies on the upload stream (a copy from
+    // pageable memory waits only for that stream's earlier work, none of
+    // which is a kernel); the main stream waits for them before the next launch
+    pdit_qap *h = r->qap;
+    const size_t mb = sizeof(int32_t) * (size_t)r->n * r->n;
+    cudaStream_t up = s->upload;
+    cudaError_t e = cudaMallocAsync(&r->ws, wsb, up);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&r->dbeta, sizeof(float) * std::max(r->sweeps, 1), up);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&r->dperm, sizeof(int32_t) * r->n, up);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&r->dcost, sizeof(int64_t), up);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&h->dD, mb, up);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&h->dF, mb, up);
+    if (e == cudaSuccess && h->cls) e = cudaMallocAsync((void **)&h->dx, (size_t)r->n, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dD, h->hD.data(), mb, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dF, h->hF.data(), mb, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess && h->cls)
+        e = cudaMemcpyAsync(h->dx, h->cls_x.data(), (size_t)r->n, cudaMemcpyHostToDevice, up);
     if (e == cudaSuccess && r->sweeps > 0)
-        e = cudaMemcpyAsync(r->dbeta, r->beta.data(), sizeof(float) * r->sweeps, cudaMemcpyHostToDevice, s->main);
+        e = cudaMemcpyAsync(r->dbeta, r->beta.data(), sizeof(float) * r->sweeps, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaEventRecord(s->uploaded, up);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PDIT_ENOMEM : cuda_fail(e, "server admit");
-    r->w = carve(r->qap, &o, r->plan, (char *)r->ws);
+    s->new_uploads = true;
+    r->w = carve(r->qap, &o, r->plan, (char *)r->ws, true);
     r->footprint = fp;
     s->used += fp;
     r->D.clear();
@@ -1783,33 +1908,87 @@ int admit(pdit_server *s, ServerRequest *r) {
     return PDIT_OK;
 }
 
-int grow(pdit_server *s, size_t ndesc, size_t nunits) {
+// Capacity of the device arrays and of host buffer b for a tick of ndesc
+// requests, nunits work units and nres finishing requests.
+int grow(pdit_server *s, TickBuf &b, size_t ndesc, size_t nunits, size_t nres) {
     if (ndesc > s->cap_desc) {
         cudaFree(s->d_descs);
-        cudaFreeHost(s->h_descs);
         cudaFree(s->d_outs);
-        cudaFreeHost(s->h_outs);
         s->d_descs = nullptr;
-        s->h_descs = nullptr;
         s->d_outs = nullptr;
-        s->h_outs = nullptr;
+        s->cap_desc = 0;
         const size_t c = std::max(ndesc, (size_t)64);
         PDIT_CK(cudaMalloc((void **)&s->d_descs, sizeof(pdit::SweepArgs) * c));
-        PDIT_CK(cudaMallocHost((void **)&s->h_descs, sizeof(pdit::SweepArgs) * c));
         PDIT_CK(cudaMalloc((void **)&s->d_outs, sizeof(BatchOut) * c));
-        PDIT_CK(cudaMallocHost((void **)&s->h_outs, sizeof(BatchOut) * c));
         s->cap_desc = c;
     }
     if (nunits > s->cap_units) {
         cudaFree(s->d_units);
-        cudaFreeHost(s->h_units);
         s->d_units = nullptr;
-        s->h_units = nullptr;
+        s->cap_units = 0;
         const size_t c = std::max(nunits * 2, (size_t)1024);
         PDIT_CK(cudaMalloc((void **)&s->d_units, sizeof(pdit::BatchUnit) * c));
-        PDIT_CK(cudaMallocHost((void **)&s->h_units, sizeof(pdit::BatchUnit) * c));
         s->cap_units = c;
     }
+    if (ndesc > b.cap_desc) {
+        cudaFreeHost(b.h_descs);
+        cudaFreeHost(b.h_outs);
+        b.h_descs = nullptr;
+        b.h_outs = nullptr;
+        b.cap_desc = 0;
+        const size_t c = std::max(ndesc, (size_t)64);
+        PDIT_CK(cudaMallocHost((void **)&b.h_descs, sizeof(pdit::SweepArgs) * c));
+        PDIT_CK(cudaMallocHost((void **)&b.h_outs, sizeof(BatchOut) * c));
+        b.cap_desc = c;
+    }
+    if (nunits > b.cap_units) {
+        cudaFreeHost(b.h_units);
+        b.h_units = nullptr;
+        b.cap_units = 0;
+        const size_t c = std::max(nunits * 2, (size_t)1024);
+        PDIT_CK(cudaMallocHost((void **)&b.h_units, sizeof(pdit::BatchUnit) * c));
+        b.cap_units = c;
+    }
+    if (nres > b.cap_res) {
+        cudaFreeHost(b.h_perm);
+        cudaFreeHost(b.h_cost);
+        b.h_perm = nullptr;
+        b.h_cost = nullptr;
+        b.cap_res = 0;
+        const size_t c = std::max(nres, (size_t)64);
+        PDIT_CK(cudaMallocHost((void **)&b.h_perm, sizeof(int32_t) * PDIT_N_MAX * c));
+        PDIT_CK(cudaMallocHost((void **)&b.h_cost, sizeof(int64_t) * c));
+        b.cap_res = c;
+    }
+    return PDIT_OK;
+}
+
+// The requests whose last slice ran in the tick of buffer b: its result
+// copies have completed (the caller checked b.done); record the results and
+// release the requests' device memory.
+void retire(pdit_server *s, TickBuf &b) {
+    const double t = now_s();
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (size_t k = 0; k < b.finishing.size(); ++k) {
+        ServerRequest *r = b.finishing[k];
+        r->perm.assign(b.h_perm + k * PDIT_N_MAX, b.h_perm + k * PDIT_N_MAX + r->n);
+        r->cost = b.h_cost[k];
+        r->t_done = t;
+        r->state = 2;
+        release_request(s, r);
+        s->completed += 1;
+    }
+    b.finishing.clear();
+    b.pending = false;
+}
+
+// Retire buffer b if its tick has completed (wait: block until it has).
+int poll(pdit_server *s, TickBuf &b, bool wait) {
+    if (!b.pending) return PDIT_OK;
+    const cudaError_t e = wait ? cudaEventSynchronize(b.done) : cudaEventQuery(b.done);
+    if (e == cudaErrorNotReady) return PDIT_OK;
+    if (e != cudaSuccess) return cuda_fail(e, "server tick");
+    retire(s, b);
     return PDIT_OK;
 }
 
@@ -1828,7 +2007,11 @@ int pdit_server_create(size_t device_budget_bytes, int slice_sweeps, int max_act
     s->max_active = max_active;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+    for (TickBuf &b : s->buf)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_queues, sizeof(int) * 64);
     if (e != cudaSuccess) {
         const int rc = cuda_fail(e, "pdit_server_create");
@@ -1841,21 +2024,30 @@ int pdit_server_create(size_t device_budget_bytes, int slice_sweeps, int max_act
 
 void pdit_server_destroy(pdit_server *s) {
     if (!s) return;
+    if (s->upload) cudaStreamSynchronize(s->upload);
     if (s->main) cudaStreamSynchronize(s->main);
     for (ServerRequest *r : s->all) {
         release_request(s, r);
         delete r;
     }
+    if (s->main) cudaStreamSynchronize(s->main);  // the releases above are stream-ordered
+    if (s->upload) cudaStreamDestroy(s->upload);
+    if (s->uploaded) cudaEventDestroy(s->uploaded);
     for (BatchClass &c : s->classes) {
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
     }
     cudaFree(s->d_descs);
-    cudaFreeHost(s->h_descs);
     cudaFree(s->d_outs);
-    cudaFreeHost(s->h_outs);
     cudaFree(s->d_units);
-    cudaFreeHost(s->h_units);
+    for (TickBuf &b : s->buf) {
+        cudaFreeHost(b.h_descs);
+        cudaFreeHost(b.h_outs);
+        cudaFreeHost(b.h_units);
+        cudaFreeHost(b.h_perm);
+        cudaFreeHost(b.h_cost);
+        if (b.done) cudaEventDestroy(b.done);
+    }
     cudaFree(s->d_queues);
     if (s->fork) cudaEventDestroy(s->fork);
     if (s->main) cudaStreamDestroy(s->main);
@@ -1888,6 +2080,11 @@ int pdit_server_submit(pdit_server *s, int n, const int32_t *D, const int32_t *F
 
 int pdit_server_tick(pdit_server *s, int *active, int *queued) {
     if (!s) return PDIT_EINVAL;
+    // 0. results of earlier ticks whose work has completed
+    for (TickBuf &b : s->buf) {
+        const int rc = poll(s, b, false);
+        if (rc) return rc;
+    }
     // 1. admit queued requests (FIFO) while slots and device memory allow
     {
         std::lock_guard<std::mutex> lock(s->mu);
@@ -1910,27 +2107,41 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
     }
     const int na = (int)s->active.size();
     if (na > 0) {
-        // 2. one slice of sweeps for every active request, one launch per kernel shape
-        size_t nunits = 0;
-        for (ServerRequest *r : s->active) nunits += (size_t)(r->replicas + r->plan.groups - 1) / r->plan.groups;
-        int rc = grow(s, (size_t)na, nunits);
+        // 2. one slice of sweeps for every active request, one launch per
+        // kernel shape; each replica's state (permutation, energies, table
+        // or permuted flow matrix) stays in the request's workspace between
+        // slices
+        TickBuf &b = s->buf[s->cur];
+        int rc = poll(s, b, true);  // the buffer's previous copies are done
+        if (rc) return rc;
+        size_t nunits = 0, nres = 0;
+        for (ServerRequest *r : s->active) {
+            nunits += (size_t)(r->replicas + r->plan.groups - 1) / r->plan.groups;
+            nres += r->done_sweeps + s->slice >= r->sweeps ? 1 : 0;
+        }
+        rc = grow(s, b, (size_t)na, nunits, nres);
         if (rc) return rc;
         std::vector<BatchClass> cls;
         std::vector<std::vector<int>> members;
+        std::vector<ServerRequest *> finishing;
+        int nout = 0;
         for (int k = 0; k < na; ++k) {
             ServerRequest *r = s->active[k];
             const Plan &p = r->plan;
-            pdit::SweepArgs &a = s->h_descs[k];
+            const int end = std::min(r->sweeps, r->done_sweeps + s->slice);
+            pdit::SweepArgs &a = b.h_descs[k];
             a = pdit::SweepArgs{};
             fill_shape(a, r->qap, p);
             a.replicas = r->replicas;
             a.sweep_begin = r->done_sweeps;
-            a.sweep_end = std::min(r->sweeps, r->done_sweeps + s->slice);
+            a.sweep_end = end;
             a.key0 = (uint32_t)r->seed;
             a.key1 = (uint32_t)(r->seed >> 32);
             a.inst = r->request_id;
             a.beta = r->dbeta;
             a.fresh = r->done_sweeps == 0 ? 1 : 0;
+            a.table_in = a.fresh ? 0 : 1;       // resume from the saved state
+            a.table_out = end < r->sweeps ? 1 : 0;  // save it for the next slice
             a.perm = r->w.perm;
             a.best_perm = r->w.best_perm;
             a.energy = r->w.energy;
@@ -1940,21 +2151,17 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
             a.rung = r->w.rung;
             a.tables = r->w.tables;
             a.status = r->w.status;
-            s->h_outs[k] = BatchOut{r->dperm, r->dcost, r->n, r->replicas, r->w.best_energy, r->w.best_perm};
+            if (end >= r->sweeps) {
+                b.h_outs[nout++] = BatchOut{r->dperm, r->dcost, r->n, r->replicas, r->w.best_energy, r->w.best_perm};
+                finishing.push_back(r);
+            }
             const int dt = r->qap->dt_bytes;
             const bool asym = r->qap->asym != 0;
             int found = -1;
             for (size_t c = 0; c < cls.size(); ++c)
                 if (same_class(cls[c], dt, asym, p)) found = (int)c;
             if (found < 0) {
-                BatchClass x;
-                x.dt = dt;
-                x.asym = asym;
-                x.maxk = p.maxk;
-                x.wpr = p.wpr;
-                x.pk = p.pk;
-                x.tsmem = p.tsmem;
-                cls.push_back(x);
+                cls.push_back(class_for(dt, asym, p));
                 members.emplace_back();
                 found = (int)cls.size() - 1;
             }
@@ -1973,14 +2180,14 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
         for (size_t c = 0; c < cls.size(); ++c) {
             std::vector<int> order = members[c];
             std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-                const ServerRequest *a = s->active[x], *b = s->active[y];
-                return (double)a->n * a->n * a->n > (double)b->n * b->n * b->n;
+                const ServerRequest *ra = s->active[x], *rb = s->active[y];
+                return (double)ra->n * ra->n * ra->n > (double)rb->n * rb->n * rb->n;
             });
             cls[c].d_units = s->d_units + u;
             const size_t u0 = u;
             for (int k : order)
                 for (int r0 = 0; r0 < s->active[k]->replicas; r0 += s->active[k]->plan.groups)
-                    s->h_units[u++] = pdit::BatchUnit{k, r0};
+                    b.h_units[u++] = pdit::BatchUnit{k, r0};
             cls[c].nunits = (int)(u - u0);
             cls[c].stream = s->classes[c].stream;
             cls[c].done = s->classes[c].done;
@@ -1990,10 +2197,17 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
             if (bps < 1 || !cls[c].tsmem) bps = 1;
             cls[c].grid = std::max(1, std::min(cls[c].nunits, s->active[members[c][0]]->qap->num_sms * bps));
         }
-        PDIT_CK(cudaMemcpyAsync(s->d_descs, s->h_descs, sizeof(pdit::SweepArgs) * na, cudaMemcpyHostToDevice, s->main));
-        PDIT_CK(cudaMemcpyAsync(s->d_units, s->h_units, sizeof(pdit::BatchUnit) * u, cudaMemcpyHostToDevice, s->main));
-        PDIT_CK(cudaMemcpyAsync(s->d_outs, s->h_outs, sizeof(BatchOut) * na, cudaMemcpyHostToDevice, s->main));
+        // from pinned host buffers: asynchronous; the device arrays are read
+        // in stream order, after the previous tick's kernels
+        PDIT_CK(cudaMemcpyAsync(s->d_descs, b.h_descs, sizeof(pdit::SweepArgs) * na, cudaMemcpyHostToDevice, s->main));
+        PDIT_CK(cudaMemcpyAsync(s->d_units, b.h_units, sizeof(pdit::BatchUnit) * u, cudaMemcpyHostToDevice, s->main));
+        if (nout > 0)
+            PDIT_CK(cudaMemcpyAsync(s->d_outs, b.h_outs, sizeof(BatchOut) * nout, cudaMemcpyHostToDevice, s->main));
         PDIT_CK(cudaMemsetAsync(s->d_queues, 0, sizeof(int) * cls.size(), s->main));
+        if (s->new_uploads) {  // the matrices and schedules of newly admitted requests
+            PDIT_CK(cudaStreamWaitEvent(s->main, s->uploaded, 0));
+            s->new_uploads = false;
+        }
         PDIT_CK(cudaEventRecord(s->fork, s->main));
         for (size_t c = 0; c < cls.size(); ++c) {
             PDIT_CK(cudaStreamWaitEvent(cls[c].stream, s->fork, 0));
@@ -2002,32 +2216,43 @@ int pdit_server_tick(pdit_server *s, int *active, int *queued) {
             PDIT_CK(cudaEventRecord(cls[c].done, cls[c].stream));
             PDIT_CK(cudaStreamWaitEvent(s->main, cls[c].done, 0));
         }
-        // 3. results of the requests whose schedule ends with this slice
-        batch_finalize_kernel<<<na, 256, 0, s->main>>>(s->d_outs);
-        PDIT_CK(cudaGetLastError());
-        std::vector<ServerRequest *> finishing;
-        for (ServerRequest *r : s->active) {
-            r->done_sweeps = std::min(r->sweeps, r->done_sweeps + s->slice);
-            if (r->done_sweeps >= r->sweeps) {
-                r->perm.resize((size_t)r->n);
-                PDIT_CK(cudaMemcpyAsync(r->perm.data(), r->dperm, sizeof(int32_t) * r->n, cudaMemcpyDeviceToHost, s->main));
-                PDIT_CK(cudaMemcpyAsync(&r->cost, r->dcost, sizeof(int64_t), cudaMemcpyDeviceToHost, s->main));
-                finishing.push_back(r);
-            }
+        // 3. results of the requests whose schedule ends with this slice,
+        // copied to pinned memory and picked up once the tick's event has
+        // completed (at a later tick)
+        if (nout > 0) {
+            batch_finalize_kernel<<<nout, 256, 0, s->main>>>(s->d_outs);
+            PDIT_CK(cudaGetLastError());
         }
-        PDIT_CK(cudaStreamSynchronize(s->main));
-        const double t = now_s();
-        std::lock_guard<std::mutex> lock(s->mu);
-        for (ServerRequest *r : finishing) {
-            r->t_done = t;
-            r->state = 2;
-            release_request(s, r);
-            s->completed += 1;
-            s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+        for (size_t k = 0; k < finishing.size(); ++k) {
+            ServerRequest *r = finishing[k];
+            PDIT_CK(cudaMemcpyAsync(b.h_perm + k * PDIT_N_MAX, r->dperm, sizeof(int32_t) * r->n,
+                                    cudaMemcpyDeviceToHost, s->main));
+            PDIT_CK(cudaMemcpyAsync(b.h_cost + k, r->dcost, sizeof(int64_t), cudaMemcpyDeviceToHost, s->main));
+        }
+        PDIT_CK(cudaEventRecord(b.done, s->main));
+        b.pending = true;
+        for (ServerRequest *r : s->active) r->done_sweeps = std::min(r->sweeps, r->done_sweeps + s->slice);
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            for (ServerRequest *r : finishing) s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+        }
+        b.finishing = std::move(finishing);
+        s->cur ^= 1;
+    } else {
+        // nothing to launch: wait for the oldest outstanding tick
+        for (int k = 1; k <= 2; ++k) {
+            TickBuf &b = s->buf[(s->cur + k) % 2];
+            if (b.pending) {
+                const int rc = poll(s, b, true);
+                if (rc) return rc;
+                break;
+            }
         }
     }
     std::lock_guard<std::mutex> lock(s->mu);
-    if (active) *active = (int)s->active.size();
+    int in_flight = 0;  // finished on the host side, results not yet picked up
+    for (const TickBuf &b : s->buf) in_flight += b.pending ? (int)b.finishing.size() : 0;
+    if (active) *active = (int)s->active.size() + in_flight;
     if (queued) *queued = (int)s->queue.size();
     return PDIT_OK;
 }

@@ -1,8 +1,9 @@
 // On-chip peaks that bound the sweep kernels, measured on the device the
 // library runs on: shared-memory load bandwidth (the binding roofline of the
-// kernels that keep their influence tables in shared memory) and the issue
-// rates of 32-bit integer multiply-add and of the 8-bit dot product dp4a
-// (the arithmetic of the influence sums and of the deferred table updates).
+// kernels that keep their working set in shared memory), the issue rates of
+// 32-bit integer multiply-add and of the 8-bit dot product dp4a (the
+// arithmetic of the influence sums and of the deferred table updates), and
+// the rates of the warp-level tensor instructions for f16 and s8 operands.
 //
 // Each probe runs one CTA of 1024 threads per SM and measures both wall time
 // (CUDA events) and SM cycles (clock64 around the timed loop, per CTA), so
@@ -85,6 +86,55 @@ __global__ void __launch_bounds__(kThreads) alu_probe_kernel(int iters, int *sin
 #pragma unroll
     for (int k = 0; k < 8; ++k) s ^= acc[k];
     if (s == 0x7F4A7C15) sink[0] = s;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+// Four independent accumulator chains per warp of the legacy warp-level
+// tensor instruction: OP 0 mma.sync m16n8k16 f16 x f16 -> f32 (2048 MACs),
+// OP 1 mma.sync m16n8k32 s8 x s8 -> s32 (4096 MACs).
+template <int OP>
+__global__ void __launch_bounds__(kThreads) mma_probe_kernel(int iters, int *sink, unsigned long long *cycles) {
+    const uint32_t a0 = 0x3C003C00u ^ threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+    const uint32_t b0 = 0x3C003C00u ^ (threadIdx.x * 7u), b1 = b0 + 5;
+    float f[4][4];
+    int c[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            f[q][e] = 0.0f;
+            c[q][e] = 0;
+        }
+    __syncthreads();
+    const unsigned long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if constexpr (OP == 0)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                        "{%8, %9}, {%0, %1, %2, %3};"
+                        : "+f"(f[q][0]), "+f"(f[q][1]), "+f"(f[q][2]), "+f"(f[q][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                else
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                        "{%8, %9}, {%0, %1, %2, %3};"
+                        : "+r"(c[q][0]), "+r"(c[q][1]), "+r"(c[q][2]), "+r"(c[q][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+            }
+        }
+    }
+    __syncthreads();
+    const unsigned long long t1 = clock64();
+    int sacc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sacc ^= c[q][e] ^ __float_as_int(f[q][e]);
+    if (sacc == 0x2545F491) sink[0] = sacc;
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
@@ -174,6 +224,20 @@ extern "C" int pdit_probe_peaks(int iters, double *out) {
             const double ops = (double)iters * 32.0 * kThreads;
             out[4] = ops * sms / t.seconds;
             out[5] = ops / t.cycles;
+        }
+    }
+    for (int op = 0; op < 2 && !rc; ++op) {
+        rc = time_probe([&](int warm) {
+            if (op == 0)
+                mma_probe_kernel<0><<<sms, kThreads, 0, st>>>(warm ? 4 : iters, (int *)dsink, dcyc);
+            else
+                mma_probe_kernel<1><<<sms, kThreads, 0, st>>>(warm ? 4 : iters, (int *)dsink, dcyc);
+        }, sms, dcyc, st, &t);
+        if (!rc) {
+            // warps per SM x instructions per warp x MACs per instruction
+            const double macs = (double)iters * 8.0 * (kThreads / 32) * (op == 0 ? 2048.0 : 4096.0);
+            out[6 + 2 * op] = macs * sms / t.seconds;
+            out[7 + 2 * op] = macs / t.cycles;
         }
     }
     if (dsink) cudaFree(dsink);

@@ -1427,5 +1427,8 @@ __host__ __device__ constexpr int dot_bound(int maxk, int wpr) {
 bool dot_shape_compiled(int maxk, int wpr);
 int dot_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks);
 int dot_launch(int maxk, int wpr, const SweepArgs &a, int grid, int threads, size_t smem, cudaStream_t stream);
+int dot_batch_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks);
+int dot_batch_launch(int maxk, int wpr, const SweepArgs *descs, const BatchUnit *units, int nunits, int *queue,
+                     int grid, int threads, size_t smem, cudaStream_t stream);
 
 }  // namespace pdit

@@ -405,11 +405,13 @@ def pdit_beta_ladder(beta_lo: float, beta_hi: float, length: int = 10) -> np.nda
 def pdit_probe_peaks(iters: int = 2000) -> dict:
     """On-chip peaks of the current device (shared-memory load bandwidth,
     dp4a and 32-bit multiply-add rates), per second and per SM clock per SM."""
-    out = np.zeros(6, dtype=np.float64)
+    out = np.zeros(10, dtype=np.float64)
     _check(lib().pdit_probe_peaks(iters, _ptr(out)), "pdit_probe_peaks")
     return {"smem_bytes_per_s": float(out[0]), "smem_bytes_per_clk_sm": float(out[1]),
             "dp4a_ops_per_s": float(out[2]), "dp4a_ops_per_clk_sm": float(out[3]),
-            "imad_ops_per_s": float(out[4]), "imad_ops_per_clk_sm": float(out[5])}
+            "imad_ops_per_s": float(out[4]), "imad_ops_per_clk_sm": float(out[5]),
+            "mma_f16_macs_per_s": float(out[6]), "mma_f16_macs_per_clk_sm": float(out[7]),
+            "mma_s8_macs_per_s": float(out[8]), "mma_s8_macs_per_clk_sm": float(out[9])}
 
 
 def pdit_beta_schedule(kind: str, sweeps: int, beta_max: float) -> np.ndarray:

@@ -40,3 +40,15 @@ def test_flow_class_bytes_per_update():
 def test_shared_memory_peak_derivation():
     # 152 SMs x 128 B/clk x 2070 MHz = 40.27 TB/s
     assert 152 * bench.SMEM_BYTES_PER_CLK * 2070e6 / 1e9 == pytest.approx(40273.92)
+
+
+def test_product_bytes_and_dp4a_per_update():
+    # N = 100: row stride 112 (16 x 7); 2 N S + 2 S + 2 N + 4 + A (12 N + 4 S + 16)
+    assert bench.product_stride(100) == 112
+    assert bench.product_stride(96) == 112   # 6 units -> 7
+    assert bench.product_stride(256) == 272  # 16 units -> 17
+    assert bench.product_stride(12) == 16
+    assert bench.product_bytes_per_update(100, 0.5) == pytest.approx(
+        22400 + 224 + 200 + 4 + 0.5 * (1200 + 448 + 16))
+    # two dot products of 28 words per candidate
+    assert bench.product_dp4a_per_update(100) == 2 * 100 * 28

@@ -1,6 +1,7 @@
 """Serving with continuous batching: requests submitted while others run,
-admitted by device-memory footprint, sliced into resumable chunks; each
-result must equal the single-instance call with instance_id = request id."""
+admitted by device-memory footprint, sliced into chunks that resume from the
+state kept on the device; each result must equal the single-instance call
+with instance_id = request id, and the CPU oracle's."""
 
 import threading
 import time
@@ -8,6 +9,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2605_24408_gb300 import instances as G
 
 pytestmark = pytest.mark.gpu
@@ -70,6 +72,13 @@ def test_results_equal_alone_and_in_the_mix(P, budget, slice_sweeps):
         aperm, acost = _alone(P, rid, replicas, sweeps, seed)
         assert cost == acost
         assert np.array_equal(perm, aperm)
+        # and the oracle's best over the same replicas (same schedule: the
+        # library's beta convention equals the oracle's bit for bit)
+        D, F = G.request_instance(rid)
+        beta = O.beta_schedule("linear", sweeps, O.beta_max(D, F))
+        r = O.anneal(D, F, beta, sweeps, seed, 0, replicas, inst=rid, threads=8)
+        assert cost == r["cost"]
+        assert np.array_equal(perm, r["perm"])
     srv.close()
 
 
@@ -89,6 +98,9 @@ def test_forms_mixed_in_one_server(P):
     for rid, (D, F) in insts.items():
         st, perm, cost, _ = srv.result(tickets[rid])
         assert st == 2
+        r = O.anneal(D, F, O.beta_schedule("linear", sweeps, O.beta_max(D, F)), sweeps, seed, 0, replicas,
+                     inst=rid, threads=8)
+        assert cost == r["cost"] and np.array_equal(perm, r["perm"])
         with P.Qap(D, F) as q:
             beta = P.pdit_beta_schedule("linear", sweeps, P.pdit_beta_max(q))
             out = P.anneal_device(q, replicas, torch.from_numpy(beta).cuda(), sweeps, seed, instance_id=rid)
@@ -112,4 +124,32 @@ def test_request_out_of_range_fails_at_admission_and_others_complete(P):
     assert srv.result(bad)[0] == 3
     st, perm, cost, _ = srv.result(good)
     assert st == 2 and sorted(perm) == list(range(D.shape[0]))
+    srv.close()
+
+
+def test_slices_resume_from_device_state_with_both_kernels(P):
+    """Requests on the dot-product kernel and on the table kernels (by a
+    table knob), sliced into many short chunks: every slice resumes from the
+    saved per-replica state, and the results equal the oracle's."""
+    rids = [120, 121, 122]
+    replicas, sweeps, seed = 16, 70, 2
+    srv = P.Server(device_budget_bytes=8 << 30, slice_sweeps=7, max_active=8)
+    tickets = {rid: srv.submit(*G.request_instance(rid), replicas, sweeps, seed, rid) for rid in rids}
+    D, F = G.dense_instance(60, seed=3)
+    tickets[500] = srv.submit(D, F, replicas, sweeps, seed, 500)
+    wide = G.random_symmetric(40, 0, 300, seed=4, tag=2)  # entries beyond a byte: table kernels
+    tickets[501] = srv.submit(wide, wide, replicas, sweeps, seed, 501)
+    while True:
+        a, q = srv.tick()
+        if a == 0 and q == 0:
+            break
+    insts = {rid: G.request_instance(rid) for rid in rids}
+    insts[500] = (D, F)
+    insts[501] = (wide, wide)
+    for rid, (Dm, Fm) in insts.items():
+        st, perm, cost, _ = srv.result(tickets[rid])
+        assert st == 2
+        r = O.anneal(Dm, Fm, O.beta_schedule("linear", sweeps, O.beta_max(Dm, Fm)), sweeps, seed, 0, replicas,
+                     inst=rid, threads=8)
+        assert cost == r["cost"] and np.array_equal(perm, r["perm"]), rid
     srv.close()
