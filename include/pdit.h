@@ -99,15 +99,17 @@ int qap_n(const pdit_qap *h);
 int pdit_set_warps_per_replica(pdit_qap *h, int wpr);
 
 /*
- * pdit_autotune -- time every compiled thread mapping (warps per replica),
- * table-update batching (1, 4 or 16 pending terms), the table placement
- * (shared or global memory, when both are possible) and, where the tables
- * live in global memory, replicas per CTA (1..4 besides the built-in choice)
- * valid for this instance on a short run of `replicas` chains over the DEVICE
- * schedule beta[sweeps] (CUDA events on the handle's stream), keep the
- * fastest for later calls on this handle and write it to shape[0] (warps per
- * replica) and shape[1] (pending terms) when shape is not NULL
- * (pdit_launch_shape reports the replicas per CTA). Synchronous; allocates and frees
+ * pdit_autotune -- time every compiled thread mapping (warps per replica) of
+ * the dot-product kernel (eligible instances; see pdit_set_influence) and of
+ * the table kernels, with their table-update batching (1, 4 or 16 pending
+ * terms), the table placement (shared or global memory, when both are
+ * possible) and, where the tables live in global memory, replicas per CTA
+ * (1..4 besides the built-in choice) valid for this instance on a short run
+ * of `replicas` chains over the DEVICE schedule beta[sweeps] (CUDA events on
+ * the handle's stream), keep the fastest for later calls on this handle and
+ * write it to shape[0] (warps per replica) and shape[1] (pending terms; 1 for
+ * the dot kernel) when shape is not NULL (pdit_launch_shape reports the
+ * replicas per CTA and which kernel). Synchronous; allocates and frees
  * small temporary buffers. Results of later calls do not depend on the
  * choice. Errors: PDIT_EINVAL, PDIT_ENOTSUP, PDIT_ECUDA.
  */

@@ -1064,19 +1064,22 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     if (!h || replicas < 1 || sweeps < 1 || !beta) return PDIT_EINVAL;
     if (!h->stream) PDIT_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     struct Knobs {
-        int place, wpr, pk, groups;
+        int place, wpr, pk, groups, infl;
     };
-    const Knobs keep{h->force_place, h->force_wpr, h->force_pk, h->force_groups};
+    const Knobs keep{h->force_place, h->force_wpr, h->force_pk, h->force_groups, h->force_infl};
     auto set = [h](const Knobs &k) {
         h->force_place = k.place;
         h->force_wpr = k.wpr;
         h->force_pk = k.pk;
         h->force_groups = k.groups;
+        h->force_infl = k.infl;
     };
     const bool cls = h->cls && h->use_cls;
     auto plan_ok = [&](const Knobs &k, Plan *p) {
         set(k);
-        return (cls ? make_class_plan(h, replicas, k.wpr, p) : make_plan(h, replicas, k.wpr, k.pk, p)) == PDIT_OK;
+        if (cls) return make_class_plan(h, replicas, k.wpr, p) == PDIT_OK;
+        if (k.infl == PDIT_INFLUENCE_PRODUCTS) return make_dot_plan(h, replicas, k.wpr, p) == PDIT_OK;
+        return make_plan(h, replicas, k.wpr, k.pk, p) == PDIT_OK;
     };
     // Candidates: the table placement (a caller's choice, else the built-in
     // one and, where that keeps the tables in shared memory, global memory),
@@ -1084,23 +1087,33 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     // the built-in choice plus 1..4 where the tables live in global memory
     // (there the built-in choice is an L2-capacity estimate). The flow-class
     // kernel keeps no table: only its warps per replica vary.
+    // The dot-product kernel (eligible instances, unless the caller fixed the
+    // table) adds its compiled warps-per-replica shapes.
     std::vector<Knobs> cand;
     const int cover = cover_for(h->n);
+    const int tbl = cls ? keep.infl : (int)PDIT_INFLUENCE_TABLE;
+    if (!cls && dot_eligible(h) && keep.infl != PDIT_INFLUENCE_TABLE)
+        for (int wpr = 1; wpr <= cover / 32 && wpr <= 8; wpr <<= 1) {
+            Plan p;
+            if (plan_ok({0, wpr, 0, 0, (int)PDIT_INFLUENCE_PRODUCTS}, &p)) cand.push_back(
+                {0, wpr, 0, 0, (int)PDIT_INFLUENCE_PRODUCTS});
+        }
     for (int place : {keep.place, (int)PDIT_PLACE_GLOBAL}) {
+        if (keep.infl == PDIT_INFLUENCE_PRODUCTS && !cls) break;
         if (place == PDIT_PLACE_GLOBAL && (keep.place != 0 || cls)) continue;
         for (int wpr = 1; wpr <= cover / 32 && wpr <= 8; wpr <<= 1)
             for (int pk : {1, 4, 16}) {
                 if (cls && pk != 1) continue;
                 Plan p;
-                if (!plan_ok({place, wpr, pk, 0}, &p)) continue;
+                if (!plan_ok({place, wpr, pk, 0, tbl}, &p)) continue;
                 if (place == PDIT_PLACE_GLOBAL) {
                     Plan q;
-                    if (plan_ok({0, wpr, pk, 0}, &q) && !q.tsmem) continue;  // already the built-in choice
+                    if (plan_ok({0, wpr, pk, 0, tbl}, &q) && !q.tsmem) continue;  // already the built-in choice
                 }
-                cand.push_back({place, wpr, pk, 0});
+                cand.push_back({place, wpr, pk, 0, tbl});
                 if (!cls && !p.tsmem)
                     for (int g = 1; g <= 4; ++g)
-                        if (g != p.groups) cand.push_back({place, wpr, pk, g});
+                        if (g != p.groups) cand.push_back({place, wpr, pk, g, tbl});
             }
     }
     int32_t *dperm = nullptr;
@@ -1148,7 +1161,7 @@ int pdit_autotune(pdit_qap *h, int replicas, const float *beta, int sweeps, int 
     set(cand[best]);
     if (shape) {
         shape[0] = cand[best].wpr;
-        shape[1] = cand[best].pk;
+        shape[1] = cand[best].infl == PDIT_INFLUENCE_PRODUCTS ? 1 : cand[best].pk;  // no pending terms
     }
     return PDIT_OK;
 }
