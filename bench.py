@@ -505,6 +505,19 @@ def run_served(args):
     t_open = time.perf_counter() - t0
     srv.close()
     lats = np.array([r[3] for r in res2 if r[1] == 2])
+    # the single-instance rate beside it: the n100 workload's shape (dense N =
+    # 100, 4096 replicas) for 1000 sweeps
+    Dn, Fn = G.named("n100")
+    with P.Qap(Dn, Fn) as qn:
+        bn = torch.from_numpy(P.pdit_beta_schedule("linear", 1000, P.pdit_beta_max(qn))).cuda()
+        P.anneal_device(qn, 4096, bn, 1000, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.anneal_device(qn, 4096, bn, 1000, 0)
+        e1.record()
+        torch.cuda.synchronize()
+        single = 100 * 4096 * 1000 / (e0.elapsed_time(e1) / 1000.0)
     line = {"metric": "p50/p99 latency, served stream", "value": float(np.percentile(lats, 50)) if len(lats) else None,
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "int32",
             "config": {"workload": "served: request r -> N uniform 20..200 (ragged generator keyed by r), "
@@ -512,7 +525,9 @@ def run_served(args):
                        "slice_sweeps": args.serve_slice, "max_active": args.serve_max_active,
                        "device_budget_gb": args.serve_budget_gb},
             "capacity": {"burst_requests": burst, "seconds": t_burst, "solves_per_s": capacity,
-                         "updates_per_s": upd / t_burst},
+                         "updates_per_s": upd / t_burst,
+                         "single_instance_n100_updates_per_s": single,
+                         "fraction_of_single_instance": upd / t_burst / single},
             "open_loop": {"arrival_rate_per_s": lam, "load_fraction_of_capacity": args.serve_load,
                           "window_s": args.serve_window, "requests": int(len(arrivals)),
                           "completed": int(len(lats)), "p50_s": float(np.percentile(lats, 50)) if len(lats) else None,
