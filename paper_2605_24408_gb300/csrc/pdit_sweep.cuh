@@ -141,10 +141,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
 // exactly, so trunc() of it is q's 24-bit significand shifted by its binary
 // exponent + 53 - k: integer operations only (a float -> uint64 conversion
 // would run on the FP64 pipe).
+// Evaluated without a branch, so that the weights of a thread's candidates
+// proceed in parallel: an x beyond 40 (or not a number) is replaced by 0 for
+// the arithmetic and its weight is zeroed at the end; every other x takes
+// exactly the operations above.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long eq5_weight(int shifted_de, float beta) {
-    const float x = __fmul_rn(__int2float_rn(shifted_de), beta);
-    if (!(x <= 40.0f)) return 0ull;
+    const float x0 = __fmul_rn(__int2float_rn(shifted_de), beta);
+    const bool live = x0 <= 40.0f;
+    const float x = live ? x0 : 0.0f;
     const float t = __fadd_rn(__fmul_rn(x, 1.44269502f), 0.5f);
     const int k = __float2int_rz(t);
     const float kf = __int2float_rn(k);
@@ -163,8 +168,8 @@ __device__ __forceinline__ unsigned long long eq5_weight(int shifted_de, float b
     const uint32_t bits = __float_as_uint(q);
     const int sh = (int)(bits >> 23) - 150 + 53 - k;
     const unsigned long long mant = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
-    if (sh >= 0) return mant << sh;
-    return sh > -24 ? (mant >> (-sh)) : 0ull;
+    const unsigned long long w = sh >= 0 ? (mant << sh) : (sh > -24 ? (mant >> (-sh)) : 0ull);
+    return live ? w : 0ull;
 }
 
 __device__ __forceinline__ int warp_min(int v) {
