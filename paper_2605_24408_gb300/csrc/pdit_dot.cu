@@ -174,150 +174,236 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
             group_sync<WPR>(bar);
             if (stop_now) break;
         }
-        const float beta = (a.mode == 1 || a.mode == 2) ? beta_fixed : a.beta[s];
+        const float beta_now = (a.mode == 1 || a.mode == 2) ? beta_fixed : a.beta[s];
+        // One p-dit update of location i with the influence entries rowv[k] =
+        // I[i][p(j)], colv[k] = I[j][p(i)] of this thread's locations j. With
+        // `fix`, rowB and colB hold the entries of the next location i + 1
+        // (computed from the same state) and are brought up to date when
+        // the update swaps, before the rows of Q move.
+        auto step = [&](const int i, const unsigned long long draw, const int (&rowv)[MAXK],
+                        const int (&colv)[MAXK], const bool fix, int (&rowB)[MAXK], int (&colB)[MAXK]) {
+            const int si = dot_slot<MAXK>(i, TA);
+            const int hi = sh[i];
+            const int8_t *Di = sD + (size_t)si * S8;
+            const int8_t *Qi = sQ + (size_t)si * S8;
+
+            // ---- swap energies (Eq. 3 in the one-term units)
+            int dc[MAXK];
+            int lmin = 0x7FFFFFFF;
+#pragma unroll
+            for (int k = 0; k < MAXK; ++k) {
+                const int j = t * MAXK + k;
+                dc[k] = 0;
+                if (active && j < n) {
+                    const int dij = Di[j];
+                    const int fab = Qi[j];  // F[p(i)][p(j)]
+                    int d = 2 * (rowv[k] - hi + colv[k] - hc[k]);
+                    if (zero_diag) {
+                        d += 4 * dij * fab;
+                    } else {
+                        const size_t sj = (size_t)(k * TA + t) * S8;
+                        d += ((int)Di[i] + (int)sD[sj + j] - 2 * dij) * ((int)Qi[i] + (int)sQ[sj + j] - 2 * fab);
+                    }
+                    if (j == i) d = 0;
+                    dc[k] = d;
+                    lmin = min(lmin, d);
+                }
+            }
+            auto fac = [&](int kk) {  // pc[kk] without indexing registers at run time
+                int v = 0;
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k)
+                    if (k == kk) v = pc[k];
+                return v;
+            };
+            const int3 sel = eq5_draw_regs<MAXK, WPR>(dc, fac, n, t, lmin, beta_now, draw, bar, gs);
+            const int js = sel.x, dstar = sel.y, fb = sel.z;
+            if (js == i) return;
+
+            // ---- apply the swap i <-> js (facilities fa = p(i), fb = p(js))
+            const int sj = dot_slot<MAXK>(js, TA);
+            const int8_t *Dj = sD + (size_t)sj * S8;
+            const int8_t *Qj = sQ + (size_t)sj * S8;
+            const int fa = sp[i];
+            const bool own_i = active && (unsigned)(i - t * MAXK) < (unsigned)MAXK;
+            const bool own_j = active && (unsigned)(js - t * MAXK) < (unsigned)MAXK;
+            // p-diagonal of the locations that keep their facility: h[m] +=
+            // (D[i][m] - D[js][m]) (F[fb][p(m)] - F[fa][p(m)]), read from the
+            // rows of Q before they move
+#pragma unroll
+            for (int k = 0; k < MAXK; ++k) {
+                const int m = t * MAXK + k;
+                if (active && m < n && m != i && m != js) {
+                    hc[k] += ((int)Di[m] - (int)Dj[m]) * ((int)Qj[m] - (int)Qi[m]);
+                    sh[m] = hc[k];
+                }
+            }
+            // the two moved entries, by the owner of js (which holds
+            // I[i][fb] = rowv and I[js][fa] = colv for it)
+            if (own_j) {
+                const int kk = js - t * MAXK;
+                int rv = 0, cv = 0;
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k)
+                    if (k == kk) {
+                        rv = rowv[k];
+                        cv = colv[k];
+                    }
+                const int hi_new = rv + ((int)Di[i] - (int)Dj[i]) * ((int)Qj[js] - (int)Qi[js]);
+                const int hj_new = cv + ((int)Di[js] - (int)Dj[js]) * ((int)Qj[i] - (int)Qi[i]);
+                sh[i] = hi_new;
+                sh[js] = hj_new;
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k)
+                    if (k == kk) {
+                        hc[k] = hj_new;
+                        pc[k] = fa;
+                    }
+            }
+            // The next location's entries under the swap tau = (i js), from
+            // the rows before they move (i' = i + 1):
+            //   I'[i'][p'(j)] = D[i'] . Q[tau j] o tau
+            //                 = rowB[tau j] + (D[i'][js] - D[i'][i]) (Q[tau j][i] - Q[tau j][js]),
+            //   I'[j][p'(i')] = D[j] . Q[tau i'] o tau
+            //                 = (colB[j], or colv[j] when js = i') + (D[j][js] - D[j][i]) (Q[tau i'][i] - Q[tau i'][js]).
+            // rowB at i and at js trade through the group scratch.
+            int fixI = 0, fixJ = 0;
+            if (fix) {
+                const int ip = i + 1;
+                const int8_t *Dip = sD + (size_t)dot_slot<MAXK>(ip, TA) * S8;
+                const int8_t *Qip = sQ + (size_t)dot_slot<MAXK>(ip, TA) * S8;
+                const int delta = (int)Dip[js] - (int)Dip[i];
+                const int qf = js != ip ? (int)Qip[i] - (int)Qip[js] : (int)Qi[i] - (int)Qi[js];
+                fixI = delta * ((int)Qj[i] - (int)Qj[js]);
+                fixJ = delta * ((int)Qi[i] - (int)Qi[js]);
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k) {
+                    const int j = t * MAXK + k;
+                    if (active && j < n) {
+                        const size_t sjk = (size_t)(k * TA + t) * S8;
+                        const int dfac = (int)sD[sjk + js] - (int)sD[sjk + i];
+                        colB[k] = (js != ip ? colB[k] : colv[k]) + dfac * qf;
+                        if (j != i && j != js) rowB[k] += delta * ((int)sQ[sjk + i] - (int)sQ[sjk + js]);
+                    }
+                }
+                if (own_j) {
+                    int v = 0;
+#pragma unroll
+                    for (int k = 0; k < MAXK; ++k)
+                        if (k == js - t * MAXK) v = rowB[k];
+                    gs->aux0 = v;  // rowB at js before the swap
+                }
+                if (own_i) {
+                    int v = 0;
+#pragma unroll
+                    for (int k = 0; k < MAXK; ++k)
+                        if (k == i - t * MAXK) v = rowB[k];
+                    gs->aux1 = v;  // rowB at i before the swap
+                }
+            }
+            group_sync<WPR>(bar);  // every read of the old rows, sp[i], sh and the scratch writes done
+            if (fix) {
+                const int bj = gs->aux0, bi = gs->aux1;
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k) {
+                    if (own_i && k == i - t * MAXK) rowB[k] = bj + fixI;
+                    if (own_j && k == js - t * MAXK) rowB[k] = bi + fixJ;
+                }
+            }
+            // rows i and js of Q trade places
+            for (int c = 16 * t; c < S8; c += 16 * G) {
+                int4 *ri = reinterpret_cast<int4 *>(sQ + (size_t)si * S8 + c);
+                int4 *rj = reinterpret_cast<int4 *>(sQ + (size_t)sj * S8 + c);
+                const int4 x = *ri;
+                *ri = *rj;
+                *rj = x;
+            }
+            if (t == 0) {
+                sp[i] = fb;
+                sp[js] = fa;
+            }
+            group_sync<WPR>(bar);
+            // then columns i and js, in every row
+            for (int row = t; row < rows; row += G) {
+                int8_t *q = sQ + (size_t)row * S8;
+                const int8_t x = q[i];
+                q[i] = q[js];
+                q[js] = x;
+            }
+            if (own_i) {
+                const int ki = i - t * MAXK;
+                const int hnew = sh[i];
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k)
+                    if (k == ki) {
+                        hc[k] = hnew;
+                        pc[k] = fb;
+                    }
+            }
+            E += dstar;
+            acc_moves += 1;
+            if (E < bestE) {
+                bestE = E;
+                bsweep = s;
+                for (int m = t; m < n; m += G) gbp[m] = sp[m];
+                if (t == 0) note_target(a, bestE, s, reached);
+            }
+            group_sync<WPR>(bar);  // Q complete before the next update's products
+        };
+
         for (int i0 = 0; i0 < n; i0 += 32) {
             // Philox(inst, replica, sweep, location) for the next 32 locations
             const uint4 rw = philox4x32_10(a.inst, grep, (uint32_t)s, (uint32_t)(i0 + lane), a.key0, a.key1);
             const int cnt = min(32, n - i0);
-            for (int ii = 0; ii < cnt; ++ii) {
+            for (int ii = 0; ii < cnt; ii += 2) {
+                // locations i and i + 1 (when it is in this batch) from one
+                // pass over this thread's rows of D and Q
                 const int i = i0 + ii;
-                const unsigned long long draw =
+                const bool two = ii + 1 < cnt;
+                int rowA[MAXK], colA[MAXK], rowB[MAXK], colB[MAXK];
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k) rowA[k] = colA[k] = rowB[k] = colB[k] = 0;
+                if (active) {
+                    const int si = dot_slot<MAXK>(i, TA);
+                    const uint32_t aDi = sD32 + (uint32_t)(si * S8), aQi = sQ32 + (uint32_t)(si * S8);
+                    if (two) {
+                        const int si1 = dot_slot<MAXK>(i + 1, TA);
+                        const uint32_t aDi1 = sD32 + (uint32_t)(si1 * S8), aQi1 = sQ32 + (uint32_t)(si1 * S8);
+#pragma unroll 1
+                        for (int c = 0; c < S8; c += 16) {  // one 16-byte chunk of every row at a time
+                            const int4 di = lds128(aDi + c), qi = lds128(aQi + c);
+                            const int4 di1 = lds128(aDi1 + c), qi1 = lds128(aQi1 + c);
+#pragma unroll
+                            for (int k = 0; k < MAXK; ++k) {
+                                const int4 qj = lds128(rowQ[k] + c), dj = lds128(rowD[k] + c);
+                                dot4(di, qj, rowA[k]);
+                                dot4(di1, qj, rowB[k]);
+                                dot4(dj, qi, colA[k]);
+                                dot4(dj, qi1, colB[k]);
+                            }
+                        }
+                    } else {
+#pragma unroll 1
+                        for (int c = 0; c < S8; c += 16) {
+                            const int4 di = lds128(aDi + c), qi = lds128(aQi + c);
+#pragma unroll
+                            for (int k = 0; k < MAXK; ++k) {
+                                dot4(di, lds128(rowQ[k] + c), rowA[k]);
+                                dot4(lds128(rowD[k] + c), qi, colA[k]);
+                            }
+                        }
+                    }
+                }
+                const unsigned long long drawA =
                     ((unsigned long long)__shfl_sync(kFull, rw.y, ii) << 32) |
                     (unsigned long long)__shfl_sync(kFull, rw.x, ii);
-                const int si = dot_slot<MAXK>(i, TA);
-                const int hi = sh[i];
-                const int8_t *Di = sD + (size_t)si * S8;
-                const int8_t *Qi = sQ + (size_t)si * S8;
-
-                // ---- influence entries: rowv[k] = I[i][p(j)], colv[k] = I[j][p(i)]
-                int rowv[MAXK], colv[MAXK];
-#pragma unroll
-                for (int k = 0; k < MAXK; ++k) rowv[k] = colv[k] = 0;
-                if (active) {
-                    const uint32_t aDi = sD32 + (uint32_t)(si * S8), aQi = sQ32 + (uint32_t)(si * S8);
-#pragma unroll 1
-                    for (int c = 0; c < S8; c += 16) {  // one 16-byte chunk of every row at a time
-                        const int4 di = lds128(aDi + c);
-                        const int4 qi = lds128(aQi + c);
-#pragma unroll
-                        for (int k = 0; k < MAXK; ++k) {
-                            dot4(di, lds128(rowQ[k] + c), rowv[k]);
-                            dot4(lds128(rowD[k] + c), qi, colv[k]);
-                        }
-                    }
+                step(i, drawA, rowA, colA, two, rowB, colB);
+                if (two) {
+                    const unsigned long long drawB =
+                        ((unsigned long long)__shfl_sync(kFull, rw.y, ii + 1) << 32) |
+                        (unsigned long long)__shfl_sync(kFull, rw.x, ii + 1);
+                    step(i + 1, drawB, rowB, colB, false, rowB, colB);
                 }
-
-                // ---- swap energies (Eq. 3 in the one-term units)
-                int dc[MAXK];
-                int lmin = 0x7FFFFFFF;
-#pragma unroll
-                for (int k = 0; k < MAXK; ++k) {
-                    const int j = t * MAXK + k;
-                    dc[k] = 0;
-                    if (active && j < n) {
-                        const int dij = Di[j];
-                        const int fab = Qi[j];  // F[p(i)][p(j)]
-                        int d = 2 * (rowv[k] - hi + colv[k] - hc[k]);
-                        if (zero_diag) {
-                            d += 4 * dij * fab;
-                        } else {
-                            const size_t sj = (size_t)(k * TA + t) * S8;
-                            d += ((int)Di[i] + (int)sD[sj + j] - 2 * dij) * ((int)Qi[i] + (int)sQ[sj + j] - 2 * fab);
-                        }
-                        if (j == i) d = 0;
-                        dc[k] = d;
-                        lmin = min(lmin, d);
-                    }
-                }
-                auto fac = [&](int kk) {  // pc[kk] without indexing registers at run time
-                    int v = 0;
-#pragma unroll
-                    for (int k = 0; k < MAXK; ++k)
-                        if (k == kk) v = pc[k];
-                    return v;
-                };
-                const int3 sel = eq5_draw_regs<MAXK, WPR>(dc, fac, n, t, lmin, beta, draw, bar, gs);
-                const int js = sel.x, dstar = sel.y, fb = sel.z;
-                if (js == i) continue;
-
-                // ---- apply the swap i <-> js (facilities fa = p(i), fb = p(js))
-                const int sj = dot_slot<MAXK>(js, TA);
-                const int8_t *Dj = sD + (size_t)sj * S8;
-                const int8_t *Qj = sQ + (size_t)sj * S8;
-                const int fa = sp[i];
-                // p-diagonal of the locations that keep their facility: h[m] +=
-                // (D[i][m] - D[js][m]) (F[fb][p(m)] - F[fa][p(m)]), read from the
-                // rows of Q before they move
-#pragma unroll
-                for (int k = 0; k < MAXK; ++k) {
-                    const int m = t * MAXK + k;
-                    if (active && m < n && m != i && m != js) {
-                        hc[k] += ((int)Di[m] - (int)Dj[m]) * ((int)Qj[m] - (int)Qi[m]);
-                        sh[m] = hc[k];
-                    }
-                }
-                // the two moved entries, by the owner of js (which holds
-                // I[i][fb] = rowv and I[js][fa] = colv for it)
-                if (active && (unsigned)(js - t * MAXK) < (unsigned)MAXK) {
-                    const int kk = js - t * MAXK;
-                    int rv = 0, cv = 0;
-#pragma unroll
-                    for (int k = 0; k < MAXK; ++k)
-                        if (k == kk) {
-                            rv = rowv[k];
-                            cv = colv[k];
-                        }
-                    const int hi_new = rv + ((int)Di[i] - (int)Dj[i]) * ((int)Qj[js] - (int)Qi[js]);
-                    const int hj_new = cv + ((int)Di[js] - (int)Dj[js]) * ((int)Qj[i] - (int)Qi[i]);
-                    sh[i] = hi_new;
-                    sh[js] = hj_new;
-#pragma unroll
-                    for (int k = 0; k < MAXK; ++k)
-                        if (k == kk) {
-                            hc[k] = hj_new;
-                            pc[k] = fa;
-                        }
-                }
-                group_sync<WPR>(bar);  // every read of the old rows, sp[i] and sh done
-                // rows i and js of Q trade places
-                for (int c = 16 * t; c < S8; c += 16 * G) {
-                    int4 *ri = reinterpret_cast<int4 *>(sQ + (size_t)si * S8 + c);
-                    int4 *rj = reinterpret_cast<int4 *>(sQ + (size_t)sj * S8 + c);
-                    const int4 x = *ri;
-                    *ri = *rj;
-                    *rj = x;
-                }
-                if (t == 0) {
-                    sp[i] = fb;
-                    sp[js] = fa;
-                }
-                group_sync<WPR>(bar);
-                // then columns i and js, in every row
-                for (int row = t; row < rows; row += G) {
-                    int8_t *q = sQ + (size_t)row * S8;
-                    const int8_t x = q[i];
-                    q[i] = q[js];
-                    q[js] = x;
-                }
-                if (active && (unsigned)(i - t * MAXK) < (unsigned)MAXK) {
-                    const int ki = i - t * MAXK;
-                    const int hnew = sh[i];
-#pragma unroll
-                    for (int k = 0; k < MAXK; ++k)
-                        if (k == ki) {
-                            hc[k] = hnew;
-                            pc[k] = fb;
-                        }
-                }
-                E += dstar;
-                acc_moves += 1;
-                if (E < bestE) {
-                    bestE = E;
-                    bsweep = s;
-                    for (int m = t; m < n; m += G) gbp[m] = sp[m];
-                    if (t == 0) note_target(a, bestE, s, reached);
-                }
-                group_sync<WPR>(bar);  // Q complete before the next update's products
             }
         }
     }

@@ -1427,7 +1427,7 @@ __host__ __device__ constexpr int class_bound(int maxk, int wpr) {
 // per replica (see that file). Shapes (MAXK, WPR) listed there. Return a
 // cudaError_t value; cudaErrorInvalidValue for a shape with no kernel.
 __host__ __device__ constexpr int dot_bound(int maxk, int wpr) {
-    return maxk == 1 ? (wpr == 1 ? 1024 : 512) : maxk == 2 ? 640 : maxk == 4 ? 512 : 384;
+    return maxk == 1 ? (wpr == 1 ? 768 : 512) : maxk <= 4 ? 512 : 384;
 }
 bool dot_shape_compiled(int maxk, int wpr);
 int dot_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks);
