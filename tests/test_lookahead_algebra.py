@@ -28,14 +28,12 @@ def test_next_location_entries_after_a_swap():
         s = int(rng.integers(0, n))
         if s == i:
             continue
-        Q = F[np.ix_(p, p)]
-        q = p.copy()
-        q[i], q[s] = q[s], q[i]
-        Q2 = F[np.ix_(q, q)]
-        assert np.array_equal(Q2, Q[np.ix_(np.where(np.arange(n) == i, s, np.where(np.arange(n) == s, i, np.arange(n))),
-                                           np.where(np.arange(n) == i, s, np.where(np.arange(n) == s, i, np.arange(n))))])
         tau = np.arange(n)
         tau[i], tau[s] = s, i
+        Q = F[np.ix_(p, p)]
+        q = p[tau]  # the swap: locations i and s trade facilities
+        Q2 = F[np.ix_(q, q)]
+        assert np.array_equal(Q2, Q[np.ix_(tau, tau)])  # rows and columns i, s exchanged
         row_b, col_b, col_a = Q @ D[ip], D @ Q[ip], D @ Q[i]
         delta = D[ip][s] - D[ip][i]
         want_row, want_col = Q2 @ D[ip], D @ Q2[ip]
