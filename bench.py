@@ -557,7 +557,7 @@ def main():
     ap.add_argument("--ragged-replicas", type=int, default=256)
     ap.add_argument("--ragged-sweeps", type=int, default=2000)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--wpr", type=int, default=0,
                     help="warps per replica (0: the library's choice)")
@@ -717,6 +717,8 @@ def main():
     hperm = torch.empty(n, dtype=torch.int32).pin_memory()
     hcost = torch.empty(1, dtype=torch.int64).pin_memory()
     e2e_t = []
+    e2e_clocks = Clocks(local)
+    e2e_clocks.start()
     for k in range(args.e2e_steps + 1):
         flush.zero_()
         torch.cuda.synchronize()
@@ -753,6 +755,7 @@ def main():
             raise SystemExit("pdit_anneal failed: %s" % P.strerror(rc))
         if k > 0:  # the first call also loads the kernels
             e2e_t.append(t1 - t0)
+    e2e_clk = e2e_clocks.stop()
     e2e_val = world * upd_rank * len(e2e_t) / sum(e2e_t) if e2e_t else None
     if e2e_t and dist is None and int(hcost[0]) != int(outs["best_cost"].item()):
         raise SystemExit("host-buffer and device-buffer results differ")
@@ -830,7 +833,9 @@ def main():
                    "launch": shape},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * n * n + 4 * len(beta),
                 "d2h_bytes_per_step": 4 * n + 8 + 4,
-                "call": "qap_create + pdit_anneal + qap_destroy from pinned host buffers"},
+                "call": "qap_create + pdit_anneal + qap_destroy from pinned host buffers",
+                "steps": len(e2e_t),
+                "clocks": {"sm_mhz": e2e_clk.get("sm_mhz"), "reasons": e2e_clk.get("reasons")}},
         # per step: sweep kernel + final reduction; PT mode: the rung set-up,
         # one sweep kernel per exchange period (4 sweeps), one exchange kernel
         # per completed period, the final reduction

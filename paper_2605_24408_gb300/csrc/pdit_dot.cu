@@ -88,20 +88,21 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
     if (a.table_in) {
         const int4 *src = reinterpret_cast<const int4 *>(reinterpret_cast<const int8_t *>(a.tables) + (size_t)r * qbytes);
         for (int idx = t; idx < (int)(qbytes / 16); idx += G) reinterpret_cast<int4 *>(sQ)[idx] = src[idx];
-    } else
-    for (int idx = t; idx < rows * W4; idx += G) {
-        const int row = idx / W4, w = idx - row * W4;
-        const int x = dot_loc<MAXK>(row, TA);
-        uint32_t word = 0;
-        if (x < n) {
-            const int32_t *Fx = a.F + (size_t)sp[x] * n;
+    } else {
+        for (int idx = t; idx < rows * W4; idx += G) {
+            const int row = idx / W4, w = idx - row * W4;
+            const int x = dot_loc<MAXK>(row, TA);
+            uint32_t word = 0;
+            if (x < n) {
+                const int32_t *Fx = a.F + (size_t)sp[x] * n;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int y = 4 * w + b;
-                if (y < n) word |= (uint32_t)(uint8_t)(int8_t)Fx[sp[y]] << (8 * b);
+                for (int b = 0; b < 4; ++b) {
+                    const int y = 4 * w + b;
+                    if (y < n) word |= (uint32_t)(uint8_t)(int8_t)Fx[sp[y]] << (8 * b);
+                }
             }
+            reinterpret_cast<uint32_t *>(sQ + (size_t)row * S8)[w] = word;
         }
-        reinterpret_cast<uint32_t *>(sQ + (size_t)row * S8)[w] = word;
     }
     group_sync<WPR>(bar);
 
