@@ -86,7 +86,7 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def survey_bytes_per_update(n: int, accept_frac: float, general: bool = False) -> float:
+def method_bytes_per_update(n: int, accept_frac: float, general: bool = False) -> float:
     """Algorithmic shared-memory bytes per p-dit update of the method as
     written (every accepted swap rewrites the table): 4 (4N) for the gathers
     (row, column, p-diagonal, permutation, int32) plus, per accepted swap,
@@ -764,7 +764,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     dt_bytes = 1 if max(abs(int(D.max())), abs(int(F.max()))) <= 127 else 2
     general = not (np.array_equal(D, D.T) and np.array_equal(F, F.T))
-    bpu = survey_bytes_per_update(n, accept_frac, general)
+    bpu = method_bytes_per_update(n, accept_frac, general)
     bpu_design = algorithmic_bytes_per_update(n, dt_bytes, accept_frac, shape["pending_swaps"], general)
     basis = (("16 N + A (8 N^2 + 16 N): the method's traffic with a rank-2 table rewrite per accepted swap "
               "(general form)") if general else

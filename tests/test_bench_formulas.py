@@ -12,10 +12,10 @@ import bench  # noqa: E402
 
 def test_method_bytes_per_update():
     # 4 (4 N) gathers + A (8 N^2 + 8 N): N = 100, A = 0.5 -> 1600 + 0.5 * 80800
-    assert bench.survey_bytes_per_update(100, 0.5) == pytest.approx(1600 + 40400)
+    assert bench.method_bytes_per_update(100, 0.5) == pytest.approx(1600 + 40400)
     # general form: four factor vectors, 16 N per accepted swap
-    assert bench.survey_bytes_per_update(100, 0.5, general=True) == pytest.approx(1600 + 0.5 * 81600)
-    assert bench.survey_bytes_per_update(256, 0.0) == 16 * 256
+    assert bench.method_bytes_per_update(100, 0.5, general=True) == pytest.approx(1600 + 0.5 * 81600)
+    assert bench.method_bytes_per_update(256, 0.0) == 16 * 256
 
 
 def test_design_bytes_per_update():
