@@ -477,6 +477,20 @@ def run_served(args):
     srv.close()
     capacity = burst / t_burst
     upd = sum(instance(rid)[0].shape[0] * R * S for rid in range(burst))
+    # the same burst as one single-instance call after another (qap_create,
+    # pdit_anneal, qap_destroy per request), each result checked against the
+    # served one
+    served = {rid: cost for rid, st, cost, _ in res}
+    t0 = time.perf_counter()
+    for rid in range(burst):
+        Dr, Fr = instance(rid)
+        with P.Qap(Dr, Fr) as qr:
+            br = torch.from_numpy(P.pdit_beta_schedule("linear", S, P.pdit_beta_max(qr))).cuda()
+            out = P.anneal_device(qr, R, br, S, 0, instance_id=rid)
+            c = int(out["best_cost"].item())
+        if c != served[rid]:
+            raise SystemExit("served and single-call results differ for request %d" % rid)
+    t_plain = time.perf_counter() - t0
     # (2) open-loop Poisson arrivals at a fraction of capacity
     lam = args.serve_load * capacity
     gaps = -np.log(1.0 - G.hash_unit(7, 91, np.arange(100000, dtype=np.uint64))) / lam
@@ -527,7 +541,10 @@ def run_served(args):
             "capacity": {"burst_requests": burst, "seconds": t_burst, "solves_per_s": capacity,
                          "updates_per_s": upd / t_burst,
                          "single_instance_n100_updates_per_s": single,
-                         "fraction_of_single_instance": upd / t_burst / single},
+                         "fraction_of_single_instance": upd / t_burst / single,
+                         "one_call_per_request_seconds": t_plain,
+                         "one_call_per_request_solves_per_s": burst / t_plain,
+                         "speedup_over_one_call_per_request": t_plain / t_burst},
             "open_loop": {"arrival_rate_per_s": lam, "load_fraction_of_capacity": args.serve_load,
                           "window_s": args.serve_window, "requests": int(len(arrivals)),
                           "completed": int(len(lats)), "p50_s": float(np.percentile(lats, 50)) if len(lats) else None,
