@@ -643,6 +643,8 @@ def main():
         P.pdit_set_table_placement(q, args.place)
     infl = {"auto": P.PDIT_INFLUENCE_AUTO, "table": P.PDIT_INFLUENCE_TABLE,
             "products": P.PDIT_INFLUENCE_PRODUCTS}[args.influence]
+    if args.mode == "cupim" and infl == P.PDIT_INFLUENCE_AUTO:
+        infl = P.PDIT_INFLUENCE_TABLE  # concurrent updates run the table kernels: report their shape
     P.pdit_set_influence(q, infl)
     pt = args.mode == "pt"
     ladder = 10
