@@ -7,9 +7,11 @@
  * (Eq. 1). Each location holds a p-dit whose state is the facility assigned
  * to it. An update of location i chooses, with the Boltzmann law of Eq. 5,
  * between staying and swapping facilities with one of the other N-1
- * locations, using the exact swap energy of Eq. 3 computed from an influence
- * table (Eq. 2) that is updated incrementally after every accepted swap. A
- * sweep updates every location once, in index order. Plain mode anneals the
+ * locations, using the exact swap energy of Eq. 3 computed from entries of
+ * the influence table (Eq. 2): kept as a table updated incrementally after
+ * every accepted swap, or formed by dot products from a permuted copy of F
+ * (pdit_set_influence); the same integers either way. A sweep updates every
+ * location once, in index order. Plain mode anneals the
  * inverse temperature beta along a per-sweep schedule; PT mode runs
  * parallel tempering (Implementation section; CPU-PIM Algorithm section).
  * Symmetric instances keep the one-term table I[m][c] = sum_j D[m][j]
@@ -63,7 +65,9 @@ extern "C" {
 #define PDIT_FLAG_RESUME 1u /* continue from the replica state already in the workspace */
 
 /* Device status bits (opts.status). */
-#define PDIT_STATUS_ENERGY_AUDIT 1 /* tracked energy != energy recomputed from the table */
+#define PDIT_STATUS_ENERGY_AUDIT 1 /* tracked energy != energy recomputed (from the table or
+                                      the flow-class vector at a resume or at the end; from
+                                      Eq. 1 at the end of every dot-kernel call) */
 
 typedef struct pdit_qap pdit_qap;
 
