@@ -202,3 +202,27 @@ def test_auto_choice_and_table_knobs():
         p.pdit_set_influence(q, p.PDIT_INFLUENCE_PRODUCTS)
         with pytest.raises(p.PditError):
             p.pdit_launch_shape(q, 64)
+
+
+def test_resume_across_kernels():
+    """A call with the dot kernel continued by the table kernels (and the
+    reverse) on the same workspace: the state the two keep between calls is
+    the same, so the continuation equals one uninterrupted oracle run."""
+    D, F = G.dense_instance(90, seed=12)
+    beta = schedule(D, F, "linear", 24)
+    p = P()
+    R = 12
+    r = O.anneal(D, F, beta, 24, 6, 0, R, threads=8)
+    for first, second in ((p.PDIT_INFLUENCE_PRODUCTS, p.PDIT_INFLUENCE_TABLE),
+                          (p.PDIT_INFLUENCE_TABLE, p.PDIT_INFLUENCE_PRODUCTS)):
+        with p.Qap(D, F) as q:
+            p.pdit_set_class_update(q, False)
+            dbeta = torch.from_numpy(beta).cuda()
+            p.pdit_set_influence(q, first)
+            a = p.anneal_device(q, R, dbeta, 24, 6, per_replica=True, sweep_end=10)
+            p.pdit_set_influence(q, second)
+            b = p.anneal_device(q, R, dbeta, 24, 6, per_replica=True, sweep_begin=10, resume=True,
+                                workspace=a["workspace"])
+            torch.cuda.synchronize()
+            g = {k: v.cpu().numpy() for k, v in b.items() if k != "workspace"}
+        check_equal(g, r)
