@@ -441,7 +441,7 @@ struct Workspace {
 // segments and tables in global memory; `persist`: any kernel whose state is
 // kept between calls by the server, the dot kernel's permuted flow matrix).
 bool needs_tables(const pdit_opts *o, const Plan &p, bool persist = false) {
-    return persist || (!p.dot && (o->mode == PDIT_MODE_PT || !p.tsmem));
+    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem);
 }
 
 Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base, bool persist = false) {
@@ -941,10 +941,13 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.sweep_begin = s;
         a.sweep_end = next;
         a.fresh = (!resume && first) ? 1 : 0;
-        // Tables persist across segments in PT mode; the global-table path
-        // always works in place.
-        a.table_in = !plan.dot && ((pt && !(first && !resume)) || (!plan.tsmem && !a.fresh && pt)) ? 1 : 0;
-        a.table_out = !plan.dot && pt ? 1 : 0;
+        // Tables (the dot kernel: permuted flow matrices) persist from one
+        // PT segment to the next within a call. The first segment of every
+        // call rebuilds them from the permutation (exact integers, so equal
+        // to what was saved), so a resumed call does not depend on which
+        // kernel or mode ran before it.
+        a.table_in = (pt && !first) ? 1 : 0;
+        a.table_out = (pt && next < se) ? 1 : 0;
         a.dump = (next == se) ? o->tables : nullptr;
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));

@@ -226,3 +226,34 @@ def test_resume_across_kernels():
             torch.cuda.synchronize()
             g = {k: v.cpu().numpy() for k, v in b.items() if k != "workspace"}
         check_equal(g, r)
+
+
+def test_pt_resume_across_kernels():
+    """Parallel tempering in two calls, the first with one kernel and the
+    second with the other; within each call the dot kernel keeps its permuted
+    flow matrices from one exchange period to the next. The rung assignment
+    and every replica's state equal one uninterrupted oracle run."""
+    D, F = G.dense_instance(64, seed=21)
+    bm = O.beta_max(D, F)
+    ladder = O.beta_schedule("geometric", 4, bm)
+    p = P()
+    R, S, cut = 12, 26, 10
+    r = O.anneal(D, F, ladder, S, 8, 0, R, threads=R, mode="pt", ladder_len=4, period=3, timeout=2)
+    kw = dict(mode=p.PDIT_MODE_PT, ladder_len=4, exchange_period=3, timeout_periods=2)
+    for first, second in ((p.PDIT_INFLUENCE_PRODUCTS, p.PDIT_INFLUENCE_TABLE),
+                          (p.PDIT_INFLUENCE_TABLE, p.PDIT_INFLUENCE_PRODUCTS),
+                          (p.PDIT_INFLUENCE_PRODUCTS, p.PDIT_INFLUENCE_PRODUCTS)):
+        with p.Qap(D, F) as q:
+            p.pdit_set_class_update(q, False)
+            dbeta = torch.from_numpy(ladder).cuda()
+            p.pdit_set_influence(q, first)
+            # room for either kernel's tables: the second call may need more
+            ws = torch.empty(1 << 24, dtype=torch.uint8, device="cuda")
+            a = p.anneal_device(q, R, dbeta, S, 8, per_replica=True, sweep_end=cut, workspace=ws, **kw)
+            p.pdit_set_influence(q, second)
+            b = p.anneal_device(q, R, dbeta, S, 8, per_replica=True, sweep_begin=cut, resume=True,
+                                workspace=a["workspace"], **kw)
+            torch.cuda.synchronize()
+            g = {k: v.cpu().numpy() for k, v in b.items() if k != "workspace"}
+        check_equal(g, r)
+        assert np.array_equal(g["replica_rung"], r["rung"])
