@@ -293,14 +293,30 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def ragged_optima():
+    """{k: optimum} for the ragged instances with N <= 12, brute-forced over
+    all N! permutations and stored under tests/golden (empty if absent)."""
+    out = {}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "ragged_optima.txt")) as fh:
+            for line in fh:
+                f = line.split()
+                if f and not line.startswith("#"):
+                    out[int(f[0])] = int(f[2])
+    except OSError:
+        pass
+    return out
+
+
 def run_ragged(args):
     """Ragged multi-instance batch: K instances, N uniform in 12..256 (half grid
     D with 30% flow density, half dense 0..99), R replicas and S linear sweeps
     each. (A) one batched, graph-captured run to the end: throughput and each
     instance's final best. Targets T_k = floor(1.01 C*_k) with C*_k the best
     cost of an independent reference run of instance k (bench_targets/
-    ragged.json: 4x replicas, 2x sweeps, another seed); without that file,
-    C*_k = the final best of run (A), said so in the line. Time to reach
+    ragged.json: 4x replicas, 2x sweeps, another seed), or for N <= 12 the
+    brute-force optimum (tests/golden/ragged_optima.txt); without those
+    files, C*_k = the final best of run (A), said so in the line. Time to reach
     every target with each instance's replicas stopping once its target is
     reached: (B) batched, (C) one single-instance launch after another."""
     import torch
@@ -374,7 +390,15 @@ def run_ragged(args):
                              "(bench_targets/ragged.json: 1024 replicas x 4000 sweeps, seed 1)")
     except (OSError, ValueError, KeyError):
         pass
-    goal = ref if ref is not None else best
+    goal = list(ref if ref is not None else best)
+    # N <= 12: the brute-force optimum over all N! permutations, where stored
+    n_exact = 0
+    for k, opt in ragged_optima().items():
+        if k < K and sizes[k] <= 12:
+            goal[k] = opt
+            n_exact += 1
+    if n_exact:
+        target_source += "; the brute-force optimum for the %d instance(s) with N <= 12" % n_exact
     # gap <= 1%: best - C* <= 0.01 C*, in integers best <= floor(1.01 C*)
     targets = [torch.tensor([c + c // 100], dtype=torch.int64, device=dev) for c in goal]
     titems = [dict(it, target=targets[k]) for k, it in enumerate(items)]

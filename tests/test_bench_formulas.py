@@ -52,3 +52,19 @@ def test_product_bytes_and_dp4a_per_update():
         22400 + 224 + 200 + 4 + 0.5 * (1200 + 448 + 16))
     # two dot products of 28 words per candidate
     assert bench.product_dp4a_per_update(100) == 2 * 100 * 28
+
+
+def test_ragged_targets_respect_the_brute_force_optima():
+    """The ragged benchmark's stored reference-run bests can be no lower than
+    the brute-force optimum of the same instance (N <= 12), and the bench
+    reads those optima as the targets of those sizes."""
+    import json
+
+    opt = bench.ragged_optima()
+    assert opt, "tests/golden/ragged_optima.txt missing"
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "bench_targets", "ragged.json")) as fh:
+        tr = {t["k"]: t for t in json.load(fh)["targets"]}
+    for k, c in opt.items():
+        assert tr[k]["n"] <= 12
+        assert tr[k]["best"] >= c
