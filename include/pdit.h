@@ -370,12 +370,12 @@ int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out);
  * serialise them.
  * First call on each device: CUDA loads this library's device code lazily
  * (the default since CUDA 12.2), so the first call on a device is the one
- * that places the 8 MiB array there, and it also looks up the array's
- * device address with that device current. A process that must not grow
- * its footprint later should make one call at start-up (or run with
- * CUDA_MODULE_LOADING=EAGER), and make that first call before any stream
- * capture. The address is kept for the life of the process: after a
- * cudaDeviceReset, calls on that device are not supported.
+ * that places the 8 MiB array there. A process that must not grow its
+ * footprint later should make one call at start-up (or run with
+ * CUDA_MODULE_LOADING=EAGER), and make that first call outside any stream
+ * capture; later calls may be captured in a CUDA graph. Every call looks up
+ * the array's device address afresh (with the caller's device current), so
+ * calls after a cudaDeviceReset use the array of the new context.
  * Errors: PDIT_EINVAL, PDIT_ENOMEM, PDIT_ENOTSUP, PDIT_ECUDA.
  */
 #define PDIT_NOALLOC_SCRATCH_BYTES (8u << 20)

@@ -1275,28 +1275,19 @@ int pdit_beta_schedule(int kind, int sweeps, double beta_max, float *out) {
 // pdit_anneal_ex keeps in a workspace) is this file-scope device array, so
 // the call never allocates device memory. In host code `g_noalloc_scratch`
 // names a host-side stand-in, not a device address: the address is taken
-// with cudaGetSymbolAddress once per device, with that device current, at
-// the first call on that device, and kept for the life of the process (a
-// device reset would move the array; calls after one are not supported).
+// with cudaGetSymbolAddress on every call, with the caller's device current
+// (a lookup once the module is loaded; taking it afresh keeps a context
+// that was torn down and recreated from writing through a stale address).
 // ---------------------------------------------------------------------------
 namespace {
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[PDIT_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[kMaxDevices] = {};
-
-int noalloc_scratch(int device, void **out) {
-    if (device < 0 || device >= kMaxDevices) return PDIT_ENOTSUP;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_noalloc_ptr[device] = p;
-    }
-    *out = g_noalloc_ptr[device];
+int noalloc_scratch(void **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = p;
     return PDIT_OK;
 }
 
@@ -1342,7 +1333,7 @@ int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas,
     const Workspace need = carve(&q, &o, plan, nullptr);
     if (need.bytes > (size_t)PDIT_NOALLOC_SCRATCH_BYTES) return PDIT_ENOMEM;
     void *scratch = nullptr;
-    rc = noalloc_scratch(q.device, &scratch);
+    rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     const Workspace w = carve(&q, &o, plan, (char *)scratch);
     cudaStream_t st = (cudaStream_t)stream;

@@ -124,3 +124,25 @@ def test_noalloc_rejects_requests_beyond_its_scratch(P):
     rc = P.pdit_anneal_noalloc(1, buf.D.data_ptr(), buf.F.data_ptr(), 4, buf.beta.data_ptr(), 4, 1,
                                buf.perm.data_ptr(), buf.cost.data_ptr(), 0, 0)
     assert rc == P.PDIT_EINVAL
+
+
+def test_noalloc_in_a_captured_graph(P):
+    """After a first call on the device, a call captured in a CUDA graph and
+    replayed gives the same result as the direct call (the captured call
+    allocates nothing and records only memsets and kernel launches)."""
+    D, F = G.named("n30")
+    beta = _schedule(P, D, F, "geometric", 120)
+    buf = _Buffers(D, F, beta)
+    buf.call(P, 64, 120, 4)
+    first = buf.result()
+    assert first[2] == 0
+    buf.perm.fill_(-1)
+    buf.cost.fill_(-1)
+    buf.status.fill_(-1)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        buf.call(P, 64, 120, 4)
+    g.replay()
+    second = buf.result()
+    assert second[1] == first[1] and np.array_equal(second[0], first[0]) and second[2] == 0
