@@ -79,6 +79,14 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def dot_kernel_name(maxk: int, wpr: int, n: int) -> str:
+    """The dot kernel instantiation a launch runs: the third parameter is the
+    row stride in 16-byte chunks where it is compiled in (four locations per
+    thread, one warp per replica, 7-chunk rows: N = 97..112), else 0."""
+    nch = 7 if (maxk, wpr) == (4, 1) and product_stride(n) == 16 * 7 else 0
+    return "dot_kernel<%d,%d,%d>" % (maxk, wpr, nch)
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -828,7 +836,7 @@ def main():
         # no table: the kernel's own traffic is the design figure; the
         # method's figure stays the basis of `achieved`
         bpu_design = product_bytes_per_update(n, accept_frac)
-        kname = "dot_kernel<%d,%d>" % (shape["candidates_per_thread"], shape["warps_per_replica"])
+        kname = dot_kernel_name(shape["candidates_per_thread"], shape["warps_per_replica"], n)
         dp4a = product_dp4a_per_update(n)
         alu = {"op": "dp4a", "per_update": dp4a, "achieved_ops_per_s": dp4a * upd_rank / kernel_s}
     achieved = bpu * upd_rank / kernel_s / 1e9

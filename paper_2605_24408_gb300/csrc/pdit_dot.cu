@@ -57,14 +57,17 @@ __device__ __forceinline__ int dot_slot(int x, int ta) {
     return (x % MAXK) * ta + x / MAXK;
 }
 
-template <int MAXK, int WPR>
+// NCH > 0: the row stride is 16 * NCH bytes, fixed at compile time, so the
+// chunk loop of the products is unrolled with constant offsets; NCH = 0 reads
+// the stride from the descriptor.
+template <int MAXK, int WPR, int NCH = 0>
 __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t, int bar, const int8_t *sD,
                                                 int8_t *sQ, int32_t *sp, int32_t *sh, GroupScratch *gs) {
     constexpr int G = 32 * WPR;
     const int lane = t & 31;
     const int wg = t >> 5;
     const int n = a.n;
-    const int S8 = a.stride;  // row stride of D and Q in bytes: 16 x odd >= n
+    const int S8 = NCH > 0 ? 16 * NCH : a.stride;  // row stride of D and Q in bytes: 16 x odd >= n
     const int W4 = S8 >> 2;   // 32-bit words per row
     const int TA = (n + MAXK - 1) / MAXK;
     const int rows = TA * MAXK;
@@ -370,8 +373,8 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
                     if (two) {
                         const int si1 = dot_slot<MAXK>(i + 1, TA);
                         const uint32_t aDi1 = sD32 + (uint32_t)(si1 * S8), aQi1 = sQ32 + (uint32_t)(si1 * S8);
-#pragma unroll 1
-                        for (int c = 0; c < S8; c += 16) {  // one 16-byte chunk of every row at a time
+                        // one 16-byte chunk of every row at a time
+                        auto chunk2 = [&](const uint32_t c) {
                             const int4 di = lds128(aDi + c), qi = lds128(aQi + c);
                             const int4 di1 = lds128(aDi1 + c), qi1 = lds128(aQi1 + c);
 #pragma unroll
@@ -382,16 +385,29 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
                                 dot4(dj, qi, colA[k]);
                                 dot4(dj, qi1, colB[k]);
                             }
+                        };
+                        if constexpr (NCH > 0) {
+#pragma unroll
+                            for (int ch = 0; ch < NCH; ++ch) chunk2(16u * ch);
+                        } else {
+#pragma unroll 1
+                            for (int c = 0; c < S8; c += 16) chunk2((uint32_t)c);
                         }
                     } else {
-#pragma unroll 1
-                        for (int c = 0; c < S8; c += 16) {
+                        auto chunk1 = [&](const uint32_t c) {
                             const int4 di = lds128(aDi + c), qi = lds128(aQi + c);
 #pragma unroll
                             for (int k = 0; k < MAXK; ++k) {
                                 dot4(di, lds128(rowQ[k] + c), rowA[k]);
                                 dot4(lds128(rowD[k] + c), qi, colA[k]);
                             }
+                        };
+                        if constexpr (NCH > 0) {
+#pragma unroll
+                            for (int ch = 0; ch < NCH; ++ch) chunk1(16u * ch);
+                        } else {
+#pragma unroll 1
+                            for (int c = 0; c < S8; c += 16) chunk1((uint32_t)c);
                         }
                     }
                 }
@@ -470,12 +486,12 @@ __device__ __forceinline__ void stage_dot_d(const int32_t *D, int n, int S8, int
 // Persistent: each group of 32 * WPR threads pulls replicas from a.queue.
 // Shared memory: D as int8 in slot order (rows x stride bytes), then per
 // group: scratch, Q (rows x stride bytes), p and h (npad int32 each).
-template <int MAXK, int WPR>
+template <int MAXK, int WPR, int NCH>
 __global__ void __launch_bounds__(dot_bound(MAXK, WPR)) dot_kernel(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int G = 32 * WPR;
     const int n = a.n;
-    const int S8 = a.stride;
+    const int S8 = NCH > 0 ? 16 * NCH : a.stride;
     const int TA = (n + MAXK - 1) / MAXK;
     const int rows = TA * MAXK;
     const int npad = (n + 3) & ~3;
@@ -495,7 +511,7 @@ __global__ void __launch_bounds__(dot_bound(MAXK, WPR)) dot_kernel(const SweepAr
         group_sync<WPR>(bar);
         const int item = gs->item;
         if (item >= a.replicas) break;
-        run_dot_replica<MAXK, WPR>(a, item, t, bar, sD, sQ, sp, sh, gs);
+        run_dot_replica<MAXK, WPR, NCH>(a, item, t, bar, sD, sQ, sp, sh, gs);
     }
 }
 
@@ -547,10 +563,10 @@ __global__ void __launch_bounds__(dot_bound(MAXK, WPR))
 
 #define PDIT_DOT_SHAPES(X) X(1, 1) X(2, 1) X(4, 1) X(8, 1) X(2, 2) X(1, 4) X(4, 2) X(2, 4) X(1, 8)
 
-template <int MAXK, int WPR>
+template <int MAXK, int WPR, int NCH = 0>
 static int dot_one(const SweepArgs &a, int grid, int threads, size_t smem, cudaStream_t st, int *blocks,
                    bool query) {
-    auto fn = dot_kernel<MAXK, WPR>;
+    auto fn = dot_kernel<MAXK, WPR, NCH>;
     if (threads > dot_bound(MAXK, WPR)) return (int)cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
@@ -561,6 +577,9 @@ static int dot_one(const SweepArgs &a, int grid, int threads, size_t smem, cudaS
 
 static int dot_dispatch(int maxk, int wpr, const SweepArgs &a, int grid, int threads, size_t smem,
                         cudaStream_t st, int *blocks, bool query) {
+    // rows of 7 chunks with four locations per thread and one warp per
+    // replica (N = 97..112): the compile-time stride
+    if (maxk == 4 && wpr == 1 && a.stride == 16 * 7) return dot_one<4, 1, 7>(a, grid, threads, smem, st, blocks, query);
 #define PDIT_DOT_CASE(MK, W) \
     if (maxk == MK && wpr == W) return dot_one<MK, W>(a, grid, threads, smem, st, blocks, query);
     PDIT_DOT_SHAPES(PDIT_DOT_CASE)
@@ -606,8 +625,9 @@ int dot_batch_launch(int maxk, int wpr, const SweepArgs *descs, const BatchUnit 
     return dot_batch_dispatch(maxk, wpr, descs, units, nunits, queue, grid, threads, smem, stream, nullptr, false);
 }
 
-int dot_blocks_per_sm(int maxk, int wpr, int threads, size_t smem, int *blocks) {
+int dot_blocks_per_sm(int maxk, int wpr, int stride, int threads, size_t smem, int *blocks) {
     SweepArgs dummy{};
+    dummy.stride = stride;
     return dot_dispatch(maxk, wpr, dummy, 0, threads, smem, nullptr, blocks, true);
 }
 

@@ -354,7 +354,7 @@ int make_dot_plan(const pdit_qap *h, int replicas, int wpr, Plan *p, size_t rese
     p->threads = 32 * wpr * g;
     p->smem = p->df_bytes + (size_t)g * p->group_bytes;
     int bps = 0;
-    const int e = pdit::dot_blocks_per_sm(p->maxk, wpr, p->threads, p->smem, &bps);
+    const int e = pdit::dot_blocks_per_sm(p->maxk, wpr, p->stride, p->threads, p->smem, &bps);
     if (e != 0) return cuda_fail((cudaError_t)e, "occupancy query");
     if (bps < 1) bps = 1;
     const int need = (replicas + g - 1) / g;

@@ -68,3 +68,11 @@ def test_ragged_targets_respect_the_brute_force_optima():
     for k, c in opt.items():
         assert tr[k]["n"] <= 12
         assert tr[k]["best"] >= c
+
+
+def test_dot_kernel_name_follows_the_compiled_strides():
+    assert bench.dot_kernel_name(4, 1, 100) == "dot_kernel<4,1,7>"
+    assert bench.dot_kernel_name(4, 1, 97) == "dot_kernel<4,1,7>"
+    assert bench.dot_kernel_name(4, 1, 113) == "dot_kernel<4,1,0>"
+    assert bench.dot_kernel_name(2, 1, 60) == "dot_kernel<2,1,0>"
+    assert bench.dot_kernel_name(1, 8, 256) == "dot_kernel<1,8,0>"
