@@ -68,6 +68,9 @@ extern "C" {
 #define PDIT_STATUS_ENERGY_AUDIT 1 /* tracked energy != energy recomputed (from the table or
                                       the flow-class vector at a resume or at the end; from
                                       Eq. 1 at the end of every dot-kernel call) */
+#define PDIT_STATUS_SCHEDULE 2     /* a part of a replica's sweeps waited past its bound for the
+                                      part before it (dot kernel, more replicas than resident
+                                      slots); the call stopped early and its results are not valid */
 
 typedef struct pdit_qap pdit_qap;
 

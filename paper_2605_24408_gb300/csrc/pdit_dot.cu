@@ -57,12 +57,61 @@ __device__ __forceinline__ int dot_slot(int x, int ta) {
     return (x % MAXK) * ta + x / MAXK;
 }
 
-// NCH > 0: the row stride is 16 * NCH bytes, fixed at compile time, so the
-// chunk loop of the products is unrolled with constant offsets; NCH = 0 reads
-// the stride from the descriptor.
-template <int MAXK, int WPR, int NCH = 0>
+// Parts done of replica r, read with acquire semantics at GPU scope.
+__device__ __forceinline__ int load_parts_done(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void publish_part(const SweepArgs &a, int r, int done) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.seg_done + r), "r"(done) : "memory");
+}
+
+// Thread 0 of a group: wait until `part` parts of replica r are published.
+// Returns 1 when they are; 0 when another group gave up (the status word
+// carries PDIT_STATUS_SCHEDULE) or this wait passes its bound (2^24 polls
+// or 20 s), which then sets that bit so that every group stops taking work.
+__device__ __forceinline__ int wait_part(const SweepArgs &a, int r, int part) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0;; ++it) {
+        if (load_parts_done(a.seg_done + r) >= part) return 1;
+        if (*reinterpret_cast<volatile int *>(a.status) & kStatusSchedule) return 0;
+        if (it >= (1u << 24) || global_ns() - t0 > 20000000000ull) {
+            atomicOr(a.status, kStatusSchedule);
+            return 0;
+        }
+        __nanosleep(256);
+    }
+}
+
+// Sweeps [begin, end) of part `part` of a call's range split into
+// a.segments parts (one part: the whole range).
+__device__ __forceinline__ int part_begin(const SweepArgs &a, int part) {
+    const int k = a.segments > 1 ? a.segments : 1;
+    return a.sweep_begin + (int)((long long)(a.sweep_end - a.sweep_begin) * part / k);
+}
+
+// Part `part` of replica r's sweeps (see part_begin). The first part starts
+// as the call says (a Fisher-Yates permutation when a.fresh, Q from the saved
+// copy when a.table_in); later parts resume from the state the previous part
+// left, Q included. The last part leaves Q as a.table_out says and runs the
+// end-of-call Eq. 1 audit. NCH > 0: the row stride is 16 * NCH bytes, fixed
+// at compile time, so the chunk loop of the products is unrolled with
+// constant offsets; NCH = 0 reads the stride from the descriptor. The state
+// a part resumes from is read through L2 (__ldcg): another SM may have
+// written it in the same launch.
+template <int MAXK, int WPR, int NCH = 0, bool PARTS = false>
 __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t, int bar, const int8_t *sD,
                                                 int8_t *sQ, int32_t *sp, int32_t *sh, GroupScratch *gs) {
+    // PARTS: the part (gs->cnt, set by the caller before a group
+    // synchronisation) and its last sweep stay in the group scratch, read
+    // where needed, rather than in registers across the sweeps; otherwise
+    // the whole call is one part
+    const int part = PARTS ? *reinterpret_cast<volatile const int *>(&gs->cnt) : 0;
+    const bool first_part = part == 0;
+    const int seg_fresh = first_part ? a.fresh : 0;
+    if (PARTS && t == 0) gs->part_end = part >= a.segments - 1 ? a.sweep_end : part_begin(a, part + 1);
     constexpr int G = 32 * WPR;
     const int lane = t & 31;
     const int wg = t >> 5;
@@ -77,10 +126,10 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
     const bool active = t < TA;  // threads t >= TA own no location
 
     // ---- permutation (sh serves as scratch for the Fisher-Yates draws)
-    if (a.fresh) {
+    if (seg_fresh) {
         fisher_yates<WPR>(a, grep, n, t, sh, sp, bar);
     } else {
-        for (int m = t; m < n; m += G) sp[m] = gp[m];
+        for (int m = t; m < n; m += G) sp[m] = __ldcg(gp + m);
     }
     group_sync<WPR>(bar);
 
@@ -88,9 +137,9 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
     // saved by the previous call on this replica (a.tables, rows x stride
     // bytes per replica)
     const size_t qbytes = (size_t)rows * S8;
-    if (a.table_in) {
+    if (first_part ? a.table_in : 1) {
         const int4 *src = reinterpret_cast<const int4 *>(reinterpret_cast<const int8_t *>(a.tables) + (size_t)r * qbytes);
-        for (int idx = t; idx < (int)(qbytes / 16); idx += G) reinterpret_cast<int4 *>(sQ)[idx] = src[idx];
+        for (int idx = t; idx < (int)(qbytes / 16); idx += G) reinterpret_cast<int4 *>(sQ)[idx] = __ldcg(src + idx);
     } else {
         for (int idx = t; idx < rows * W4; idx += G) {
             const int row = idx / W4, w = idx - row * W4;
@@ -140,7 +189,7 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
     long long E, bestE, acc_moves;
     int bsweep;
     bool reached = false;
-    if (a.fresh) {
+    if (seg_fresh) {
         E = esum;
         bestE = esum;
         bsweep = -1;
@@ -148,14 +197,15 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
         for (int m = t; m < n; m += G) gbp[m] = sp[m];
         if (t == 0) note_target(a, bestE, -1, reached);
     } else {
-        E = a.energy[r];
-        bestE = a.best_energy[r];
-        bsweep = a.best_sweep[r];
-        acc_moves = a.accepted[r];
+        E = __ldcg(a.energy + r);
+        bestE = __ldcg(a.best_energy + r);
+        bsweep = __ldcg(a.best_sweep + r);
+        acc_moves = __ldcg(a.accepted + r);
         if (E != esum && t == 0) atomicOr(a.status, 1);
     }
     group_sync<WPR>(bar);
 
+    const int s_begin = part_begin(a, part);
     const float beta_fixed = a.sweep_end <= a.sweep_begin ? 0.0f
                            : a.mode == 1 ? a.beta[a.rung[r]] : a.mode == 2 ? a.beta[r] : 0.0f;
     const int zero_diag = a.zero_diag;
@@ -169,7 +219,7 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
         rowQ[k] = sQ32 + (uint32_t)((k * TA + t) * S8);
     }
 
-    for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
+    for (int s = s_begin; s < (PARTS ? *reinterpret_cast<volatile const int *>(&gs->part_end) : a.sweep_end); ++s) {
         if (a.stop) {
             // group-uniform decision from one read of the instance's flag
             if (t == 0) gs->stop = *reinterpret_cast<volatile int *>(a.done);
@@ -425,26 +475,30 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
         }
     }
 
-    // ---- audit: Eq. 1 of the final permutation, from D and the global F,
-    // equals the tracked energy
-    long long eq1 = 0;
-    for (int x = t; x < n; x += G) {
-        const int8_t *Dx = sD + (size_t)dot_slot<MAXK>(x, TA) * S8;
-        const int32_t *Fx = a.F + (size_t)sp[x] * n;
-        long long acc = 0;
-        for (int y = 0; y < n; ++y) acc += (long long)Dx[y] * Fx[sp[y]];
-        eq1 += acc;
-    }
-    eq1 = warp_sum(eq1);
-    if constexpr (WPR > 1) {
-        group_sync<WPR>(bar);
-        if (lane == 0) gs->wtot[wg] = (unsigned long long)eq1;
-        group_sync<WPR>(bar);
-        eq1 = 0;
+    // ---- audit (the last unit of a call): Eq. 1 of the final permutation,
+    // from D and the global F, equals the tracked energy
+    const int part_now = PARTS ? *reinterpret_cast<volatile const int *>(&gs->cnt) : 0;
+    const bool last_part = !PARTS || part_now >= a.segments - 1;
+    if (last_part) {
+        long long eq1 = 0;
+        for (int x = t; x < n; x += G) {
+            const int8_t *Dx = sD + (size_t)dot_slot<MAXK>(x, TA) * S8;
+            const int32_t *Fx = a.F + (size_t)sp[x] * n;
+            long long acc = 0;
+            for (int y = 0; y < n; ++y) acc += (long long)Dx[y] * Fx[sp[y]];
+            eq1 += acc;
+        }
+        eq1 = warp_sum(eq1);
+        if constexpr (WPR > 1) {
+            group_sync<WPR>(bar);
+            if (lane == 0) gs->wtot[wg] = (unsigned long long)eq1;
+            group_sync<WPR>(bar);
+            eq1 = 0;
 #pragma unroll
-        for (int w = 0; w < WPR; ++w) eq1 += (long long)gs->wtot[w];
+            for (int w = 0; w < WPR; ++w) eq1 += (long long)gs->wtot[w];
+        }
+        if (t == 0 && eq1 != E) atomicOr(a.status, 1);
     }
-    if (t == 0 && eq1 != E) atomicOr(a.status, 1);
 
     // ---- write back
     for (int m = t; m < n; m += G) gp[m] = sp[m];
@@ -454,11 +508,15 @@ __device__ __forceinline__ void run_dot_replica(const SweepArgs &a, int r, int t
         a.best_sweep[r] = bsweep;
         a.accepted[r] = acc_moves;
     }
-    if (a.table_out) {
+    if (last_part ? a.table_out : 1) {
         int4 *dst = reinterpret_cast<int4 *>(reinterpret_cast<int8_t *>(a.tables) + (size_t)r * qbytes);
         for (int idx = t; idx < (int)(qbytes / 16); idx += G) dst[idx] = reinterpret_cast<const int4 *>(sQ)[idx];
     }
+    // A call split into parts: publish this part once every thread's writes
+    // of the replica's state are visible device-wide.
+    if (PARTS) __threadfence();
     group_sync<WPR>(bar);
+    if (PARTS && t == 0) publish_part(a, r, part_now + 1);
 }
 
 // D of an n-location instance as int8 rows in slot order (rows x stride
@@ -483,10 +541,10 @@ __device__ __forceinline__ void stage_dot_d(const int32_t *D, int n, int S8, int
     }
 }
 
-// Persistent: each group of 32 * WPR threads pulls replicas from a.queue.
+// Persistent: each group of 32 * WPR threads pulls work units from a.queue.
 // Shared memory: D as int8 in slot order (rows x stride bytes), then per
 // group: scratch, Q (rows x stride bytes), p and h (npad int32 each).
-template <int MAXK, int WPR, int NCH>
+template <int MAXK, int WPR, int NCH, bool PARTS>
 __global__ void __launch_bounds__(dot_bound(MAXK, WPR)) dot_kernel(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int G = 32 * WPR;
@@ -506,12 +564,43 @@ __global__ void __launch_bounds__(dot_bound(MAXK, WPR)) dot_kernel(const SweepAr
     int8_t *sQ = reinterpret_cast<int8_t *>(gb + kScratchBytes);
     int32_t *sp = reinterpret_cast<int32_t *>(gb + kScratchBytes + (size_t)rows * S8);
     int32_t *sh = sp + npad;
+    if constexpr (!PARTS) {
+        // one unit per replica: the whole call
+        for (;;) {
+            if (t == 0) gs->item = atomicAdd(a.queue, 1);
+            group_sync<WPR>(bar);
+            const int item = gs->item;
+            if (item >= a.replicas) break;
+            run_dot_replica<MAXK, WPR, NCH, false>(a, item, t, bar, sD, sQ, sp, sh, gs);
+        }
+        return;
+    }
+    // Work units in order (part k of every replica, then part k + 1): part k
+    // of replica r starts once part k - 1 has been published. That part was
+    // taken `replicas` units earlier by a group that is running, so the wait
+    // ends (it is bounded all the same).
+    const int K = a.segments > 1 ? a.segments : 1;
+    const long long units = (long long)a.replicas * K;
     for (;;) {
-        if (t == 0) gs->item = atomicAdd(a.queue, 1);
+        if (t == 0) {
+            // thread 0 splits the unit into (part, replica) and waits for
+            // the previous part; the group reads the replica, the part and
+            // whether to go on from the scratch
+            const int item = atomicAdd(a.queue, 1);
+            int go = item < units ? 1 : 0, part = 0, r = item;
+            if (go && K > 1) {
+                part = item / a.replicas;
+                r = item - part * a.replicas;
+                if (part > 0) go = wait_part(a, r, part);
+            }
+            gs->item = r;
+            gs->cnt = part;
+            gs->stop = go;
+        }
         group_sync<WPR>(bar);
-        const int item = gs->item;
-        if (item >= a.replicas) break;
-        run_dot_replica<MAXK, WPR, NCH>(a, item, t, bar, sD, sQ, sp, sh, gs);
+        const int go = gs->stop, r = gs->item;
+        if (!go) break;
+        run_dot_replica<MAXK, WPR, NCH, true>(a, r, t, bar, sD, sQ, sp, sh, gs);
     }
 }
 
@@ -566,7 +655,9 @@ __global__ void __launch_bounds__(dot_bound(MAXK, WPR))
 template <int MAXK, int WPR, int NCH = 0>
 static int dot_one(const SweepArgs &a, int grid, int threads, size_t smem, cudaStream_t st, int *blocks,
                    bool query) {
-    auto fn = dot_kernel<MAXK, WPR, NCH>;
+    // calls split into parts run their own instantiation, so that whole
+    // calls keep the registers of the plain loop
+    auto fn = a.segments > 1 ? dot_kernel<MAXK, WPR, NCH, true> : dot_kernel<MAXK, WPR, NCH, false>;
     if (threads > dot_bound(MAXK, WPR)) return (int)cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;

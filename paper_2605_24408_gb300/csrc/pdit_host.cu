@@ -432,16 +432,33 @@ int batch_plan(const pdit_qap *h, Plan *p, size_t reserve) {
 }
 
 struct Workspace {
-    int32_t *perm, *best_perm, *best_sweep, *rung, *since_top, *queue, *status, *tables, *done;
+    int32_t *perm, *best_perm, *best_sweep, *rung, *since_top, *queue, *status, *tables, *done, *seg_done;
     int64_t *energy, *best_energy, *accepted;
     size_t bytes;
 };
 
+// Parts a dot-kernel call splits every replica's sweeps into (anneal and
+// fixed modes). With more replicas than resident slots, whole anneals leave
+// the last round's idle slots idle until it ends (at n100, 4096 replicas in
+// 2432 slots ran at 0.85 of the full-round rate); parts of at least 8
+// sweeps, run as separate work units in one launch, keep every slot busy
+// to the end. 1 when the replicas fill whole rounds.
+int dot_parts(const pdit_opts *o, const Plan &p) {
+    if (!p.dot || (o->mode != PDIT_MODE_ANNEAL && o->mode != PDIT_MODE_FIXED)) return 1;
+    const long long slots = (long long)p.grid * p.groups;
+    if (o->replicas <= slots || o->replicas % slots == 0) return 1;
+    const int span = (o->sweep_end < 0 ? o->sweeps : o->sweep_end) - o->sweep_begin;
+    long long k = std::min(16, span / 8);
+    k = std::min<long long>(k, 0x7FFFFFFFll / o->replicas);
+    return (int)std::max<long long>(1, k);
+}
+
 // Whether the workspace holds every replica's table (the table kernels: PT
 // segments and tables in global memory; `persist`: any kernel whose state is
-// kept between calls by the server, the dot kernel's permuted flow matrix).
+// kept between calls by the server, the dot kernel's permuted flow matrix;
+// the dot kernel's Q between the parts of a call).
 bool needs_tables(const pdit_opts *o, const Plan &p, bool persist = false) {
-    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem);
+    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem) || dot_parts(o, p) > 1;
 }
 
 Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base, bool persist = false) {
@@ -465,6 +482,7 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.queue = (int32_t *)take(4 * 64);
     w.status = (int32_t *)take(4);
     w.done = (int32_t *)take(4);
+    w.seg_done = dot_parts(o, p) > 1 ? (int32_t *)take(4 * R) : nullptr;
     w.tables = needs_tables(o, p, persist) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
     w.bytes = off;
     return w;
@@ -931,6 +949,8 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.reach_sweep = o->reach_sweep;
     a.done = o->target ? w.done : nullptr;
     a.stop = (o->target && o->stop_at_target) ? 1 : 0;
+    a.segments = dot_parts(o, plan);
+    a.seg_done = w.seg_done;
 
     // Segments: the whole range in anneal mode; exchange periods in PT mode.
     bool first = true;
@@ -951,6 +971,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.dump = (next == se) ? o->tables : nullptr;
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
+            if (a.segments > 1) PDIT_CK(cudaMemsetAsync(w.seg_done, 0, sizeof(int32_t) * R, st));
             const int e = plan.cls ? class_launch(h->dt_bytes, plan, a, st)
                         : plan.dot ? pdit::dot_launch(plan.maxk, plan.wpr, a, plan.grid, plan.threads, plan.smem, st)
                                    : sweep_launch(h->dt_bytes, h->asym != 0, plan, a, st);

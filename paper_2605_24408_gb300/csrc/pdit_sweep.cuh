@@ -81,6 +81,12 @@ struct SweepArgs {
     int32_t *dump;         // optional [replicas][n][n]: final tables
     int *queue;            // work counter, zero at launch
     int *status;           // audit bits
+    // dot kernel, anneal and fixed modes: each replica's sweep range split
+    // into `segments` consecutive parts run as separate work units (1: one
+    // unit per replica); seg_done[r] = parts of replica r finished, zero at
+    // launch
+    int segments;
+    int *seg_done;
     // time-to-target bookkeeping (all optional, per instance)
     const int64_t *target;      // record the first time best <= *target
     unsigned long long *reach_ns;  // atomicMin of %globaltimer at that moment
@@ -98,12 +104,18 @@ struct SweepArgs {
 struct GroupScratch {
     unsigned long long wtot[8];
     int wmin[8];
-    int sel_jf, sel_d, sel_pad;  // the drawn outcome: location | facility << 16, energy change
+    int sel_jf, sel_d;  // the drawn outcome: location | facility << 16, energy change
+    int part_end;       // dot kernel: the last sweep (exclusive) of the part being run
     int item;
     int stop;
-    int cnt, aux0, aux1;
+    int cnt;            // concurrent updates: accepted swaps; dot kernel: the part being run
+    int aux0, aux1;
 };
 constexpr size_t kScratchBytes = sizeof(GroupScratch);  // 128
+
+// Status bit: a wait for the previous part of a replica passed its bound
+// (the value of PDIT_STATUS_SCHEDULE).
+constexpr int kStatusSchedule = 2;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10, from its published definition (Salmon, Moraes, Dror and

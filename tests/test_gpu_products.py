@@ -257,3 +257,61 @@ def test_pt_resume_across_kernels():
             g = {k: v.cpu().numpy() for k, v in b.items() if k != "workspace"}
         check_equal(g, r)
         assert np.array_equal(g["replica_rung"], r["rung"])
+
+
+def _slots(p, q):
+    """Resident replica slots of the dot kernel on this GPU (CTAs x replicas
+    per CTA when the replicas exceed what fits at once)."""
+    shape = p.pdit_launch_shape(q, 1 << 20)
+    return shape["ctas"] * shape["replicas_per_cta"]
+
+
+@pytest.mark.parametrize("n,S,kind", [(40, 40, "linear"), (100, 24, "geometric"), (13, 16, "linear")])
+def test_more_replicas_than_slots_runs_in_parts(n, S, kind):
+    """With more replicas than resident slots (not a whole number of rounds)
+    each replica's sweeps run as several work units of one launch, each part
+    resuming from the state the previous part published. Replicas of the
+    first and of the last round equal the oracle's."""
+    D, F = G.dense_instance(n, seed=n + 11)
+    beta = schedule(D, F, kind, S)
+    p = P()
+    with p.Qap(D, F) as q:
+        p.pdit_set_class_update(q, False)
+        p.pdit_set_influence(q, p.PDIT_INFLUENCE_PRODUCTS)
+        R = _slots(p, q) + 37
+        dbeta = torch.from_numpy(beta).cuda()
+        out = p.anneal_device(q, R, dbeta, S, 5, per_replica=True)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
+    for lo, hi in [(0, 3), (R - 40, R - 37), (R - 3, R)]:
+        r = O.anneal(D, F, beta, S, 5, lo, hi, threads=3)
+        check_equal(g, r, slice(lo, hi))
+    assert int(g["best_cost"][0]) <= int(g["replica_best_cost"].min())
+
+
+def test_parts_with_resume_and_fixed_beta():
+    """Parts inside a resumed call (the range [sweep_begin, sweep_end) split)
+    and in fixed-beta mode: still the oracle's results."""
+    D, F = G.dense_instance(48, seed=3)
+    p = P()
+    S = 30
+    beta = schedule(D, F, "linear", S)
+    with p.Qap(D, F) as q:
+        p.pdit_set_class_update(q, False)
+        R = _slots(p, q) + 5
+        dbeta = torch.from_numpy(beta).cuda()
+        a = p.anneal_device(q, R, dbeta, S, 9, per_replica=True, sweep_end=17)
+        b = p.anneal_device(q, R, dbeta, S, 9, per_replica=True, sweep_begin=17, resume=True,
+                            workspace=a["workspace"])
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in b.items() if k != "workspace"}
+        bm = O.beta_max(D, F)
+        fb = np.array([bm * (0.2 + 0.01 * (i % 50)) for i in range(R)], np.float32)
+        f = p.anneal_device(q, R, torch.from_numpy(fb).cuda(), 16, 4, per_replica=True, mode=p.PDIT_MODE_FIXED)
+        torch.cuda.synchronize()
+        gf = {k: v.cpu().numpy() for k, v in f.items() if k != "workspace"}
+    for lo, hi in [(0, 2), (R - 2, R)]:
+        r = O.anneal(D, F, beta, S, 9, lo, hi, threads=2)
+        check_equal(g, r, slice(lo, hi))
+        rf = O.anneal(D, F, fb[lo:hi], 16, 4, lo, hi, threads=2, mode="fixed")  # beta of the k-th replica
+        check_equal(gf, rf, slice(lo, hi))
