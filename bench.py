@@ -79,12 +79,22 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def dot_kernel_name(maxk: int, wpr: int, n: int) -> str:
+def dot_parts(replicas: int, slots: int, sweeps: int) -> int:
+    """Parts the library splits each replica's sweeps into for one
+    dot-kernel call in anneal or fixed mode: 1 while the replicas fill whole
+    rounds of the resident slots, else up to 16 parts of at least 8 sweeps."""
+    if replicas <= slots or replicas % slots == 0:
+        return 1
+    return max(1, min(16, sweeps // 8, 0x7FFFFFFF // replicas))
+
+
+def dot_kernel_name(maxk: int, wpr: int, n: int, parts: int = 1) -> str:
     """The dot kernel instantiation a launch runs: the third parameter is the
     row stride in 16-byte chunks where it is compiled in (four locations per
-    thread, one warp per replica, 7-chunk rows: N = 97..112), else 0."""
+    thread, one warp per replica, 7-chunk rows: N = 97..112), else 0; the
+    fourth is 1 for a call split into parts."""
     nch = 7 if (maxk, wpr) == (4, 1) and product_stride(n) == 16 * 7 else 0
-    return "dot_kernel<%d,%d,%d>" % (maxk, wpr, nch)
+    return "dot_kernel<%d,%d,%d,%d>" % (maxk, wpr, nch, 1 if parts > 1 else 0)
 
 
 def host_cores() -> int:
@@ -836,7 +846,8 @@ def main():
         # no table: the kernel's own traffic is the design figure; the
         # method's figure stays the basis of `achieved`
         bpu_design = product_bytes_per_update(n, accept_frac)
-        kname = dot_kernel_name(shape["candidates_per_thread"], shape["warps_per_replica"], n)
+        parts = 1 if pt else dot_parts(replicas, shape["ctas"] * shape["replicas_per_cta"], sweeps)
+        kname = dot_kernel_name(shape["candidates_per_thread"], shape["warps_per_replica"], n, parts)
         dp4a = product_dp4a_per_update(n)
         alu = {"op": "dp4a", "per_update": dp4a, "achieved_ops_per_s": dp4a * upd_rank / kernel_s}
     achieved = bpu * upd_rank / kernel_s / 1e9

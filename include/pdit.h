@@ -311,7 +311,11 @@ void pdit_opts_init(pdit_opts *o);
  * The workspace holds every replica's state between calls (permutation,
  * energy, best-so-far, counters, and in PT mode the influence tables), so a
  * call with PDIT_FLAG_RESUME continues exactly where the previous one
- * stopped.
+ * stopped. With the dot-product kernel in anneal or fixed mode and more
+ * replicas than the GPU holds at once (not a whole number of rounds), each
+ * replica's sweeps run as up to 16 parts in one launch; the workspace then
+ * also holds every replica's permuted flow matrix (about n * n bytes) and a
+ * part counter (4 bytes). Results do not depend on the parts.
  */
 size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o);
 

@@ -71,8 +71,18 @@ def test_ragged_targets_respect_the_brute_force_optima():
 
 
 def test_dot_kernel_name_follows_the_compiled_strides():
-    assert bench.dot_kernel_name(4, 1, 100) == "dot_kernel<4,1,7>"
-    assert bench.dot_kernel_name(4, 1, 97) == "dot_kernel<4,1,7>"
-    assert bench.dot_kernel_name(4, 1, 113) == "dot_kernel<4,1,0>"
-    assert bench.dot_kernel_name(2, 1, 60) == "dot_kernel<2,1,0>"
-    assert bench.dot_kernel_name(1, 8, 256) == "dot_kernel<1,8,0>"
+    assert bench.dot_kernel_name(4, 1, 100) == "dot_kernel<4,1,7,0>"
+    assert bench.dot_kernel_name(4, 1, 97, parts=16) == "dot_kernel<4,1,7,1>"
+    assert bench.dot_kernel_name(4, 1, 113) == "dot_kernel<4,1,0,0>"
+    assert bench.dot_kernel_name(2, 1, 60) == "dot_kernel<2,1,0,0>"
+    assert bench.dot_kernel_name(1, 8, 256) == "dot_kernel<1,8,0,0>"
+
+
+def test_dot_parts_rule():
+    # n100: 4096 replicas in 2432 slots, 10000 sweeps -> 16 parts
+    assert bench.dot_parts(4096, 2432, 10000) == 16
+    assert bench.dot_parts(4096, 2432, 20) == 2      # parts of at least 8 sweeps
+    assert bench.dot_parts(4096, 2432, 7) == 1
+    assert bench.dot_parts(2432, 2432, 10000) == 1   # one whole round
+    assert bench.dot_parts(4864, 2432, 10000) == 1   # two whole rounds
+    assert bench.dot_parts(100, 2432, 10000) == 1
