@@ -79,13 +79,15 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def dot_parts(replicas: int, slots: int, sweeps: int) -> int:
+def dot_parts(replicas: int, slots: int, sweeps: int, pt: bool = False) -> int:
     """Parts the library splits each replica's sweeps into for one
-    dot-kernel call in anneal or fixed mode: 1 while the replicas fill whole
-    rounds of the resident slots, else up to 16 parts of at least 8 sweeps."""
+    dot-kernel launch of `sweeps` sweeps: 1 while the replicas fill whole
+    rounds of the resident slots, else up to 16 parts of at least 8 sweeps
+    (anneal and fixed modes) or of one sweep (a PT launch, one exchange
+    period)."""
     if replicas <= slots or replicas % slots == 0:
         return 1
-    return max(1, min(16, sweeps // 8, 0x7FFFFFFF // replicas))
+    return max(1, min(16, sweeps if pt else sweeps // 8, 0x7FFFFFFF // replicas))
 
 
 def dot_kernel_name(maxk: int, wpr: int, n: int, parts: int = 1) -> str:
@@ -846,7 +848,7 @@ def main():
         # no table: the kernel's own traffic is the design figure; the
         # method's figure stays the basis of `achieved`
         bpu_design = product_bytes_per_update(n, accept_frac)
-        parts = 1 if pt else dot_parts(replicas, shape["ctas"] * shape["replicas_per_cta"], sweeps)
+        parts = dot_parts(replicas, shape["ctas"] * shape["replicas_per_cta"], 4 if pt else sweeps, pt)
         kname = dot_kernel_name(shape["candidates_per_thread"], shape["warps_per_replica"], n, parts)
         dp4a = product_dp4a_per_update(n)
         alu = {"op": "dp4a", "per_update": dp4a, "achieved_ops_per_s": dp4a * upd_rank / kernel_s}

@@ -437,20 +437,28 @@ struct Workspace {
     size_t bytes;
 };
 
-// Parts a dot-kernel call splits every replica's sweeps into (anneal and
-// fixed modes). With more replicas than resident slots, whole anneals leave
-// the last round's idle slots idle until it ends (at n100, 4096 replicas in
-// 2432 slots ran at 0.85 of the full-round rate); parts of at least 8
-// sweeps, run as separate work units in one launch, keep every slot busy
-// to the end. 1 when the replicas fill whole rounds.
-int dot_parts(const pdit_opts *o, const Plan &p) {
-    if (!p.dot || (o->mode != PDIT_MODE_ANNEAL && o->mode != PDIT_MODE_FIXED)) return 1;
+// Parts a dot-kernel launch of `span` sweeps splits every replica's sweeps
+// into. With more replicas than resident slots, whole units leave the last
+// round's idle slots idle until it ends (at n100, 4096 replicas in 2432
+// slots ran at 0.85 of the full-round rate); parts run as separate work
+// units of the one launch keep every slot busy to the end. Anneal and fixed
+// modes: up to 16 parts of at least 8 sweeps; PT launches (one exchange
+// period each): up to 16 parts of one sweep. 1 when the replicas fill whole
+// rounds.
+int dot_parts_of(const pdit_opts *o, const Plan &p, int span) {
+    if (!p.dot || o->mode == PDIT_MODE_CUPIM) return 1;
     const long long slots = (long long)p.grid * p.groups;
     if (o->replicas <= slots || o->replicas % slots == 0) return 1;
-    const int span = (o->sweep_end < 0 ? o->sweeps : o->sweep_end) - o->sweep_begin;
-    long long k = std::min(16, span / 8);
+    long long k = std::min(16, o->mode == PDIT_MODE_PT ? span : span / 8);
     k = std::min<long long>(k, 0x7FFFFFFFll / o->replicas);
     return (int)std::max<long long>(1, k);
+}
+
+// The most parts any launch of the call uses.
+int dot_parts(const pdit_opts *o, const Plan &p) {
+    const int se = o->sweep_end < 0 ? o->sweeps : o->sweep_end;
+    const int span = o->mode == PDIT_MODE_PT ? std::min(o->exchange_period, se - o->sweep_begin) : se - o->sweep_begin;
+    return dot_parts_of(o, p, span);
 }
 
 // Whether the workspace holds every replica's table (the table kernels: PT
@@ -949,7 +957,6 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
     a.reach_sweep = o->reach_sweep;
     a.done = o->target ? w.done : nullptr;
     a.stop = (o->target && o->stop_at_target) ? 1 : 0;
-    a.segments = dot_parts(o, plan);
     a.seg_done = w.seg_done;
 
     // Segments: the whole range in anneal mode; exchange periods in PT mode.
@@ -969,6 +976,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.table_in = (pt && !first) ? 1 : 0;
         a.table_out = (pt && next < se) ? 1 : 0;
         a.dump = (next == se) ? o->tables : nullptr;
+        a.segments = dot_parts_of(o, plan, next - s);
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
             if (a.segments > 1) PDIT_CK(cudaMemsetAsync(w.seg_done, 0, sizeof(int32_t) * R, st));

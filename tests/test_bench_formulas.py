@@ -86,3 +86,4 @@ def test_dot_parts_rule():
     assert bench.dot_parts(2432, 2432, 10000) == 1   # one whole round
     assert bench.dot_parts(4864, 2432, 10000) == 1   # two whole rounds
     assert bench.dot_parts(100, 2432, 10000) == 1
+    assert bench.dot_parts(4090, 2432, 4, pt=True) == 4  # one exchange period, parts of one sweep

@@ -315,3 +315,27 @@ def test_parts_with_resume_and_fixed_beta():
         check_equal(g, r, slice(lo, hi))
         rf = O.anneal(D, F, fb[lo:hi], 16, 4, lo, hi, threads=2, mode="fixed")  # beta of the k-th replica
         check_equal(gf, rf, slice(lo, hi))
+
+
+def test_parallel_tempering_in_parts():
+    """Parallel tempering with more replicas than slots: each exchange
+    period's launch runs every replica's sweeps as one-sweep parts. Ladders
+    of the first and of the last round, with their rungs, equal the
+    oracle's."""
+    D, F = G.dense_instance(40, seed=17)
+    bm = O.beta_max(D, F)
+    L = 5
+    ladder = O.beta_schedule("geometric", L, bm)
+    p = P()
+    S = 13
+    with p.Qap(D, F) as q:
+        p.pdit_set_class_update(q, False)
+        R = -(-(_slots(p, q) + 37) // L) * L
+        out = p.anneal_device(q, R, torch.from_numpy(ladder).cuda(), S, 3, per_replica=True,
+                              mode=p.PDIT_MODE_PT, ladder_len=L, exchange_period=4, timeout_periods=2)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
+    for lo, hi in [(0, L), (R - L, R)]:
+        r = O.anneal(D, F, ladder, S, 3, lo, hi, threads=L, mode="pt", ladder_len=L, period=4, timeout=2)
+        check_equal(g, r, slice(lo, hi))
+        assert np.array_equal(g["replica_rung"][lo:hi], r["rung"])
