@@ -57,41 +57,6 @@ __device__ __forceinline__ int dot_slot(int x, int ta) {
     return (x % MAXK) * ta + x / MAXK;
 }
 
-// Parts done of replica r, read with acquire semantics at GPU scope.
-__device__ __forceinline__ int load_parts_done(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void publish_part(const SweepArgs &a, int r, int done) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.seg_done + r), "r"(done) : "memory");
-}
-
-// Thread 0 of a group: wait until `part` parts of replica r are published.
-// Returns 1 when they are; 0 when another group gave up (the status word
-// carries PDIT_STATUS_SCHEDULE) or this wait passes its bound (2^24 polls
-// or 20 s), which then sets that bit so that every group stops taking work.
-__device__ __forceinline__ int wait_part(const SweepArgs &a, int r, int part) {
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 0;; ++it) {
-        if (load_parts_done(a.seg_done + r) >= part) return 1;
-        if (*reinterpret_cast<volatile int *>(a.status) & kStatusSchedule) return 0;
-        if (it >= (1u << 24) || global_ns() - t0 > 20000000000ull) {
-            atomicOr(a.status, kStatusSchedule);
-            return 0;
-        }
-        __nanosleep(256);
-    }
-}
-
-// Sweeps [begin, end) of part `part` of a call's range split into
-// a.segments parts (one part: the whole range).
-__device__ __forceinline__ int part_begin(const SweepArgs &a, int part) {
-    const int k = a.segments > 1 ? a.segments : 1;
-    return a.sweep_begin + (int)((long long)(a.sweep_end - a.sweep_begin) * part / k);
-}
-
 // Part `part` of replica r's sweeps (see part_begin). The first part starts
 // as the call says (a Fisher-Yates permutation when a.fresh, Q from the saved
 // copy when a.table_in); later parts resume from the state the previous part

@@ -437,16 +437,18 @@ struct Workspace {
     size_t bytes;
 };
 
-// Parts a dot-kernel launch of `span` sweeps splits every replica's sweeps
-// into. With more replicas than resident slots, whole units leave the last
-// round's idle slots idle until it ends (at n100, 4096 replicas in 2432
-// slots ran at 0.85 of the full-round rate); parts run as separate work
-// units of the one launch keep every slot busy to the end. Anneal and fixed
-// modes: up to 16 parts of at least 8 sweeps; PT launches (one exchange
-// period each): up to 16 parts of one sweep. 1 when the replicas fill whole
-// rounds.
-int dot_parts_of(const pdit_opts *o, const Plan &p, int span) {
-    if (!p.dot || o->mode == PDIT_MODE_CUPIM) return 1;
+// Parts a launch of `span` sweeps of the dot or table kernels splits every
+// replica's sweeps into. With more replicas than resident slots, whole units
+// leave the last round's idle slots idle until it ends (at n100, 4096
+// replicas in 2432 slots ran at 0.85 of the full-round rate; the general
+// form's table kernel, 4096 in 760 slots, at 0.94); parts run as separate
+// work units of the one launch keep every slot busy to the end. Anneal,
+// fixed and concurrent modes: up to 16 parts of at least 8 sweeps; PT
+// launches (one exchange period each): up to 16 parts of one sweep. 1 when
+// the replicas fill whole rounds, for the flow-class kernel and for tables
+// in global memory.
+int parts_of(const pdit_opts *o, const Plan &p, int span) {
+    if (p.cls || (!p.dot && !p.tsmem)) return 1;  // global-table kernels take whole calls
     const long long slots = (long long)p.grid * p.groups;
     if (o->replicas <= slots || o->replicas % slots == 0) return 1;
     long long k = std::min(16, o->mode == PDIT_MODE_PT ? span : span / 8);
@@ -455,18 +457,18 @@ int dot_parts_of(const pdit_opts *o, const Plan &p, int span) {
 }
 
 // The most parts any launch of the call uses.
-int dot_parts(const pdit_opts *o, const Plan &p) {
+int call_parts(const pdit_opts *o, const Plan &p) {
     const int se = o->sweep_end < 0 ? o->sweeps : o->sweep_end;
     const int span = o->mode == PDIT_MODE_PT ? std::min(o->exchange_period, se - o->sweep_begin) : se - o->sweep_begin;
-    return dot_parts_of(o, p, span);
+    return parts_of(o, p, span);
 }
 
 // Whether the workspace holds every replica's table (the table kernels: PT
 // segments and tables in global memory; `persist`: any kernel whose state is
 // kept between calls by the server, the dot kernel's permuted flow matrix;
-// the dot kernel's Q between the parts of a call).
+// either kernel's table between the parts of a launch).
 bool needs_tables(const pdit_opts *o, const Plan &p, bool persist = false) {
-    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem) || dot_parts(o, p) > 1;
+    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem) || call_parts(o, p) > 1;
 }
 
 Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base, bool persist = false) {
@@ -490,7 +492,7 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.queue = (int32_t *)take(4 * 64);
     w.status = (int32_t *)take(4);
     w.done = (int32_t *)take(4);
-    w.seg_done = dot_parts(o, p) > 1 ? (int32_t *)take(4 * R) : nullptr;
+    w.seg_done = call_parts(o, p) > 1 ? (int32_t *)take(4 * R) : nullptr;
     w.tables = needs_tables(o, p, persist) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
     w.bytes = off;
     return w;
@@ -976,7 +978,7 @@ int pdit_anneal_ex(pdit_qap *h, const pdit_opts *o) {
         a.table_in = (pt && !first) ? 1 : 0;
         a.table_out = (pt && next < se) ? 1 : 0;
         a.dump = (next == se) ? o->tables : nullptr;
-        a.segments = dot_parts_of(o, plan, next - s);
+        a.segments = parts_of(o, plan, next - s);
         if (!(first && resume && s == se)) {
             PDIT_CK(cudaMemsetAsync(w.queue, 0, sizeof(int32_t), st));
             if (a.segments > 1) PDIT_CK(cudaMemsetAsync(w.seg_done, 0, sizeof(int32_t) * R, st));

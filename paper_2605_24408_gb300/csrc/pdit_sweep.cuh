@@ -408,6 +408,46 @@ __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
 }
 
 // ---------------------------------------------------------------------------
+// Calls split into parts (more replicas than resident slots): each part of a
+// replica's sweeps is a work unit; a part starts once the replica's previous
+// part is published.
+// ---------------------------------------------------------------------------
+// Parts done of replica r, read with acquire semantics at GPU scope.
+__device__ __forceinline__ int load_parts_done(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void publish_part(const SweepArgs &a, int r, int done) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.seg_done + r), "r"(done) : "memory");
+}
+
+// Thread 0 of a group: wait until `part` parts of replica r are published.
+// Returns 1 when they are; 0 when another group gave up (the status word
+// carries PDIT_STATUS_SCHEDULE) or this wait passes its bound (2^24 polls
+// or 20 s), which then sets that bit so that every group stops taking work.
+__device__ __forceinline__ int wait_part(const SweepArgs &a, int r, int part) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0;; ++it) {
+        if (load_parts_done(a.seg_done + r) >= part) return 1;
+        if (*reinterpret_cast<volatile int *>(a.status) & kStatusSchedule) return 0;
+        if (it >= (1u << 24) || global_ns() - t0 > 20000000000ull) {
+            atomicOr(a.status, kStatusSchedule);
+            return 0;
+        }
+        __nanosleep(256);
+    }
+}
+
+// First sweep of part `part` when a launch's range [sweep_begin, sweep_end)
+// is split into a.segments parts (one part: the whole range).
+__device__ __forceinline__ int part_begin(const SweepArgs &a, int part) {
+    const int k = a.segments > 1 ? a.segments : 1;
+    return a.sweep_begin + (int)((long long)(a.sweep_end - a.sweep_begin) * part / k);
+}
+
+// ---------------------------------------------------------------------------
 // One replica: initial state, table build, sweeps [sweep_begin, sweep_end),
 // write-back. `T` is the replica's influence table (shared or global memory),
 // row stride S; sp = permutation, sh = p-diagonal h[m] = I[m][p(m)],
@@ -418,11 +458,21 @@ __device__ __forceinline__ void add_scaled(int4 &x, int u, const int4 &v) {
 // held before the table is rewritten (1 = immediate updates); a swap is one
 // term, or two in the general form (ASYM).
 // ---------------------------------------------------------------------------
+//
+// `part`: which part of the launch's sweep range this unit runs when the
+// range is split into a.segments parts (see part_begin; 0 with a.segments
+// <= 1: the whole range). Later parts resume from the state the previous
+// part left (the table included) and publish their own at the end. Tables
+// in global memory (TG) are never split: their kernels keep the plain loop
+// (the part bookkeeping slowed the N = 256 kernel by 4-6% even where it
+// took no parts, for a 2% gain from parts).
 template <typename DT, int MAXK, int WPR, int PK, bool TG = false, bool ASYM = false>
-__device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, int bar,
+__device__ __forceinline__ void run_replica(const SweepArgs &a, int part_arg, int r, int t, int bar,
                                             const DT *sD, const DT *sF, int32_t *T, int32_t *sp,
                                             int32_t *sh, int32_t *sv, uint32_t *upk,
                                             uint32_t *vpk, GroupScratch *gs) {
+    constexpr bool PARTS = !TG;
+    const int part = PARTS ? part_arg : 0;
     constexpr int G = 32 * WPR;
     constexpr int ROWS = WPR * MAXK;       // table rows per lane in the rank-1 update (32-row slots)
     constexpr int QB = ROWS <= 4 ? 2 : 1;  // table quads per batch of the rank-1 update
@@ -441,23 +491,25 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     int32_t *gp = a.perm + (size_t)r * n;
     int32_t *gbp = a.best_perm + (size_t)r * n;
 
-    // ---- permutation
-    if (a.fresh) {
+    const int fresh = part == 0 ? a.fresh : 0;
+    // ---- permutation (a resumed state is read through L2: another SM may
+    // have written it in the same launch)
+    if (fresh) {
         fisher_yates<WPR>(a, grep, n, t, sv, sp, bar);
     } else {
-        for (int m = t; m < n; m += G) sp[m] = gp[m];
+        for (int m = t; m < n; m += G) sp[m] = PARTS ? __ldcg(gp + m) : gp[m];
     }
     group_sync<WPR>(bar);
 
     // ---- influence table, Eq. 2 in the one-term form I[m][c] = sum_j D[m][j] F[c][p(j)]
     // (F symmetric, so row p(j) of F is read contiguously); general form:
     // both terms of Eq. 2, T[m][c] = sum_j D[m][j] F[c][p(j)] + D[j][m] F[p(j)][c].
-    if (a.table_in) {
+    if (part == 0 ? a.table_in : 1) {
         const int32_t *src = a.tables + (size_t)r * n * S;
         if (src != T) {
             const int4 *s4 = reinterpret_cast<const int4 *>(src);
             int4 *d4 = reinterpret_cast<int4 *>(T);
-            for (int idx = t; idx < n * S / 4; idx += G) d4[idx] = s4[idx];
+            for (int idx = t; idx < n * S / 4; idx += G) d4[idx] = PARTS ? __ldcg(s4 + idx) : s4[idx];
         }
     } else {
         for (int m = 0; m < n; ++m) {
@@ -501,7 +553,7 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
     long long E, bestE, acc_moves;
     int bsweep;
     bool reached = false;
-    if (a.fresh) {
+    if (fresh) {
         E = esum;
         bestE = esum;
         bsweep = -1;
@@ -509,14 +561,28 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
         for (int m = t; m < n; m += G) gbp[m] = sp[m];
         if (t == 0) note_target(a, bestE, -1, reached);
     } else {
-        E = a.energy[r];
-        bestE = a.best_energy[r];
-        bsweep = a.best_sweep[r];
-        acc_moves = a.accepted[r];
+        if constexpr (PARTS) {
+            E = __ldcg(a.energy + r);
+            bestE = __ldcg(a.best_energy + r);
+            bsweep = __ldcg(a.best_sweep + r);
+            acc_moves = __ldcg(a.accepted + r);
+        } else {
+            E = a.energy[r];
+            bestE = a.best_energy[r];
+            bsweep = a.best_sweep[r];
+            acc_moves = a.accepted[r];
+        }
         if (E != esum && t == 0) atomicOr(a.status, 1);
     }
     group_sync<WPR>(bar);
 
+    // the part's sweeps (its last sweep stays in the group scratch, read at
+    // every sweep, rather than in a register across the sweeps)
+    const int s_begin = PARTS ? part_begin(a, part) : a.sweep_begin;
+    if constexpr (PARTS) {
+        if (t == 0) gs->part_end = part >= a.segments - 1 ? a.sweep_end : part_begin(a, part + 1);
+        group_sync<WPR>(bar);
+    }
     const float beta_fixed = a.sweep_end <= a.sweep_begin ? 0.0f
                            : a.mode == 1 ? a.beta[a.rung[r]] : a.mode == 2 ? a.beta[r] : 0.0f;
     const int zero_diag = a.zero_diag;
@@ -822,7 +888,16 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
         if (a.mode != 3 && a.sweep_begin < a.sweep_end) prefetch(0);
     }
 
-    for (int s = a.sweep_begin; s < a.sweep_end; ++s) {
+    // (an if-constexpr function: a conditional expression with the volatile
+    // read in its untaken arm changed the global-table kernels' register
+    // allocation and cost them 4-9%)
+    auto sweep_end_now = [&]() {
+        if constexpr (PARTS)
+            return *reinterpret_cast<volatile const int *>(&gs->part_end);
+        else
+            return a.sweep_end;
+    };
+    for (int s = s_begin; s < sweep_end_now(); ++s) {
         if (a.stop) {
             // group-uniform decision from one read of the instance's flag
             if (t == 0) gs->stop = *reinterpret_cast<volatile int *>(a.done);
@@ -1186,7 +1261,8 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
         a.best_sweep[r] = bsweep;
         a.accepted[r] = acc_moves;
     }
-    if (a.table_out) {
+    const bool last_part = !PARTS || part >= a.segments - 1;
+    if (last_part ? a.table_out : 1) {
         int32_t *dst = a.tables + (size_t)r * n * S;
         if (dst != T) {
             const int4 *s4 = reinterpret_cast<const int4 *>(T);
@@ -1194,11 +1270,16 @@ __device__ __forceinline__ void run_replica(const SweepArgs &a, int r, int t, in
             for (int idx = t; idx < n * S / 4; idx += G) d4[idx] = s4[idx];
         }
     }
-    if (a.dump) {
+    if (a.dump && last_part) {
         int32_t *dst = a.dump + (size_t)r * n * n;
         for (int idx = t; idx < n * n; idx += G) dst[idx] = T[(idx / n) * S + idx % n];
     }
+    // a launch split into parts: publish this part once every thread's
+    // writes of the replica's state are visible device-wide
+    const bool publish = PARTS && a.segments > 1;
+    if (publish) __threadfence();
     group_sync<WPR>(bar);
+    if (publish && t == 0) publish_part(a, r, part + 1);
 }
 
 // Largest CTA each instantiation is compiled for; it caps the registers per
@@ -1253,18 +1334,43 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads) sweep_kernel(
     int32_t *sv = sh + npad;
     uint32_t *upk = reinterpret_cast<uint32_t *>(sv + a.sv_len);  // [PK / 4][npad], PK > 1 only
     uint32_t *vpk = upk + (PK / 4) * npad;
-    for (;;) {
-        if (t == 0) gs->item = atomicAdd(a.queue, 1);
-        group_sync<WPR>(bar);
-        const int item = gs->item;
-        if (item >= a.replicas) break;
-        if constexpr (TSMEM) {
-            run_replica<DT, MAXK, WPR, PK, false, ASYM>(a, item, t, bar, sD, sF, sT, sp, sh, sv, upk, vpk, gs);
-        } else {
-            run_replica<DT, MAXK, WPR, PK, true, ASYM>(a, item, t, bar, sD, sF,
+    if constexpr (!TSMEM) {
+        // tables in global memory: one unit per replica, the whole call
+        for (;;) {
+            if (t == 0) gs->item = atomicAdd(a.queue, 1);
+            group_sync<WPR>(bar);
+            const int item = gs->item;
+            if (item >= a.replicas) break;
+            run_replica<DT, MAXK, WPR, PK, true, ASYM>(a, 0, item, t, bar, sD, sF,
                                                        a.tables + (size_t)item * n * a.stride, sp, sh, sv, upk,
                                                        vpk, gs);
         }
+        return;
+    }
+    // Work units in order: part k of every replica, then part k + 1 (one
+    // part: one unit per replica). Part k of replica r starts once part k - 1
+    // is published; that part was taken `replicas` units earlier by a group
+    // that is running, so the wait ends (it is bounded all the same).
+    const int K = a.segments > 1 ? a.segments : 1;
+    const long long units = (long long)a.replicas * K;
+    for (;;) {
+        if (t == 0) {
+            const int item = atomicAdd(a.queue, 1);
+            int go = item < units ? 1 : 0, part = 0, r = item;
+            if (go && K > 1) {
+                part = item / a.replicas;
+                r = item - part * a.replicas;
+                if (part > 0) go = wait_part(a, r, part);
+            }
+            gs->item = r;
+            gs->sel_jf = part;
+            gs->stop = go;
+        }
+        group_sync<WPR>(bar);
+        const int go = gs->stop, r = gs->item, part = gs->sel_jf;
+        group_sync<WPR>(bar);  // the scratch words are reused by the update
+        if (!go) break;
+        run_replica<DT, MAXK, WPR, PK, false, ASYM>(a, part, r, t, bar, sD, sF, sT, sp, sh, sv, upk, vpk, gs);
     }
 }
 
@@ -1325,7 +1431,7 @@ __global__ void __launch_bounds__(SweepBounds<MAXK, WPR>::threads)
             uint32_t *upk = reinterpret_cast<uint32_t *>(sv + sa.sv_len);
             uint32_t *vpk = upk + (PK / 4) * npad;
             int32_t *T = TSMEM ? sT : sa.tables + (size_t)r * n * sa.stride;
-            run_replica<DT, MAXK, WPR, PK, !TSMEM, ASYM>(sa, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
+            run_replica<DT, MAXK, WPR, PK, !TSMEM, ASYM>(sa, 0, r, t, bar, sD, sF, T, sp, sh, sv, upk, vpk, gs);
         }
     }
 }

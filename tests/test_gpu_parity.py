@@ -403,3 +403,34 @@ def test_very_many_replicas_sampled():
         assert np.array_equal(g["replica_best_cost"][sl], r["best_cost"])
         assert np.array_equal(g["replica_accepted"][sl], r["accepted"])
     assert int(g["best_cost"][0]) == int(g["replica_best_cost"].min())
+
+
+# --- launches split into parts (more replicas than resident slots) ----------
+
+@pytest.mark.parametrize("kind,n,mode,S", [("sym", 40, 0, 24), ("asym", 36, 0, 24), ("sym", 40, 3, 24),
+                                           ("sym", 200, 0, 16), ("asym", 150, 0, 16)])
+def test_table_kernels_in_parts(kind, n, mode, S):
+    """The table kernels with more replicas than resident slots. With tables
+    in shared memory each replica's sweeps run as parts (work units of one
+    launch) that resume from the state, table included, the previous part
+    published; tables in global memory (N = 150, 200) take whole calls.
+    Replicas of the first and of the last round, their final tables
+    included, equal the oracle's; symmetric and general form, sequential and
+    concurrent updates."""
+    D, F = (G.dense_instance(n, seed=n + 5) if kind == "sym" else G.asymmetric_instance(n, seed=n + 5))
+    beta = schedule(D, F, "linear", S)
+    p = P()
+    with p.Qap(D, F) as q:
+        p.pdit_set_influence(q, p.PDIT_INFLUENCE_TABLE)
+        shape = p.pdit_launch_shape(q, 1 << 20)
+        R = shape["ctas"] * shape["replicas_per_cta"] + 7
+        dbeta = torch.from_numpy(beta).cuda()
+        out = p.anneal_device(q, R, dbeta, S, 2, per_replica=True, tables=True, mode=mode)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
+    m = {0: "anneal", 3: "cupim"}[mode]
+    for lo, hi in [(0, 2), (R - 9, R - 7), (R - 2, R)]:
+        r = O.anneal(D, F, beta, S, 2, lo, hi, threads=2, tables=True, mode=m)
+        if r["general"]:
+            r["tables"] = -r["tables"]  # the oracle keeps Eq. 2's sign; the kernels its negation
+        check_equal(g, r, slice(lo, hi), tables=True)
