@@ -83,11 +83,12 @@ def dot_parts(replicas: int, slots: int, sweeps: int, pt: bool = False) -> int:
     """Parts the library splits each replica's sweeps into for one
     dot-kernel launch of `sweeps` sweeps: 1 while the replicas fill whole
     rounds of the resident slots, else up to 16 parts of at least 8 sweeps
-    (anneal and fixed modes) or of one sweep (a PT launch, one exchange
-    period)."""
+    (anneal and fixed modes; more where a part would exceed 1000 sweeps) or
+    of one sweep (a PT launch, one exchange period)."""
     if replicas <= slots or replicas % slots == 0:
         return 1
-    return max(1, min(16, sweeps if pt else sweeps // 8, 0x7FFFFFFF // replicas))
+    k = max(min(16, sweeps if pt else sweeps // 8), -(-sweeps // 1000))  # parts of at most 1000 sweeps
+    return max(1, min(k, (1 << 30) // replicas))
 
 
 def dot_kernel_name(maxk: int, wpr: int, n: int, parts: int = 1) -> str:

@@ -452,7 +452,12 @@ int parts_of(const pdit_opts *o, const Plan &p, int span) {
     const long long slots = (long long)p.grid * p.groups;
     if (o->replicas <= slots || o->replicas % slots == 0) return 1;
     long long k = std::min(16, o->mode == PDIT_MODE_PT ? span : span / 8);
-    k = std::min<long long>(k, 0x7FFFFFFFll / o->replicas);
+    // parts of at most 1000 sweeps, so that a part's wait for the one
+    // before it stays far inside its bound however long the call
+    k = std::max<long long>(k, (span + 999) / 1000);
+    // the unit counter (int32, taken once more by every group at the end)
+    // stays below 2^30
+    k = std::min<long long>(k, (1ll << 30) / o->replicas);
     return (int)std::max<long long>(1, k);
 }
 

@@ -425,18 +425,21 @@ __device__ __forceinline__ void publish_part(const SweepArgs &a, int r, int done
 
 // Thread 0 of a group: wait until `part` parts of replica r are published.
 // Returns 1 when they are; 0 when another group gave up (the status word
-// carries PDIT_STATUS_SCHEDULE) or this wait passes its bound (2^24 polls
-// or 20 s), which then sets that bit so that every group stops taking work.
+// carries PDIT_STATUS_SCHEDULE) or this wait passes its bound, which then
+// sets that bit so that every group stops taking work. The bound is 2^26
+// polls about 1 us apart (roughly a minute, against parts of at most 1000
+// sweeps that last well under a second); it counts polls rather than wall
+// time, so a context that the GPU time-slices with others does not run out
+// of it while nothing of its own runs.
 __device__ __forceinline__ int wait_part(const SweepArgs &a, int r, int part) {
-    const unsigned long long t0 = global_ns();
     for (unsigned it = 0;; ++it) {
         if (load_parts_done(a.seg_done + r) >= part) return 1;
         if (*reinterpret_cast<volatile int *>(a.status) & kStatusSchedule) return 0;
-        if (it >= (1u << 24) || global_ns() - t0 > 20000000000ull) {
+        if (it >= (1u << 26)) {
             atomicOr(a.status, kStatusSchedule);
             return 0;
         }
-        __nanosleep(256);
+        __nanosleep(1000);
     }
 }
 

@@ -87,3 +87,4 @@ def test_dot_parts_rule():
     assert bench.dot_parts(4864, 2432, 10000) == 1   # two whole rounds
     assert bench.dot_parts(100, 2432, 10000) == 1
     assert bench.dot_parts(4090, 2432, 4, pt=True) == 4  # one exchange period, parts of one sweep
+    assert bench.dot_parts(4096, 2432, 100000) == 100    # parts of at most 1000 sweeps
