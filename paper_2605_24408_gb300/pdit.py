@@ -41,6 +41,8 @@ PDIT_MODE_PT = 1
 PDIT_MODE_FIXED = 2
 PDIT_MODE_CUPIM = 3
 PDIT_FLAG_RESUME = 1
+PDIT_STATUS_ENERGY_AUDIT = 1
+PDIT_STATUS_SCHEDULE = 2
 PDIT_BATCH_STOP_AT_TARGET = 1
 PDIT_BATCH_GRAPH = 2
 

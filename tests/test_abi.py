@@ -110,3 +110,23 @@ def test_header_compiles_as_c99_and_links(tmp_path, L):
            "-Wl,-rpath," + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_constants_match_the_header():
+    """Every PDIT_* constant of the Python binding has the value the C header
+    defines (the header is the ABI; the binding restates it)."""
+    import re
+
+    from paper_2605_24408_gb300 import pdit
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "include", "pdit.h")) as fh:
+        text = fh.read()
+    defs = {}
+    for name, value in re.findall(r"^#define\s+(PDIT_[A-Z0-9_]+)\s+\(?(-?[0-9]+)u?\)?", text, re.M):
+        defs[name] = int(value)
+    names = [n for n in dir(pdit) if re.fullmatch(r"PDIT_[A-Z0-9_]+", n) and isinstance(getattr(pdit, n), int)]
+    assert len(names) >= 20
+    for n in names:
+        assert n in defs, n
+        assert getattr(pdit, n) == defs[n], n
