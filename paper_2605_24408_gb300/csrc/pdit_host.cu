@@ -447,10 +447,19 @@ struct Workspace {
 // launches (one exchange period each): up to 16 parts of one sweep. 1 when
 // the replicas fill whole rounds, for the flow-class kernel and for tables
 // in global memory.
-int parts_of(const pdit_opts *o, const Plan &p, int span) {
-    if (p.cls || (!p.dot && !p.tsmem)) return 1;  // global-table kernels take whole calls
+// Whether launches of the plan may be split (the replicas exceed the slots
+// and are not a whole number of rounds; dot kernel or tables in shared
+// memory). It does not depend on the sweep range, so neither does the
+// workspace: a resumed call over a longer range fits the workspace of the
+// call before it.
+bool may_split(const pdit_opts *o, const Plan &p) {
+    if (p.cls || (!p.dot && !p.tsmem)) return false;  // global-table kernels take whole calls
     const long long slots = (long long)p.grid * p.groups;
-    if (o->replicas <= slots || o->replicas % slots == 0) return 1;
+    return o->replicas > slots && o->replicas % slots != 0;
+}
+
+int parts_of(const pdit_opts *o, const Plan &p, int span) {
+    if (!may_split(o, p)) return 1;
     long long k = std::min(16, o->mode == PDIT_MODE_PT ? span : span / 8);
     // parts of at most 1000 sweeps, so that a part's wait for the one
     // before it stays far inside its bound however long the call
@@ -461,19 +470,12 @@ int parts_of(const pdit_opts *o, const Plan &p, int span) {
     return (int)std::max<long long>(1, k);
 }
 
-// The most parts any launch of the call uses.
-int call_parts(const pdit_opts *o, const Plan &p) {
-    const int se = o->sweep_end < 0 ? o->sweeps : o->sweep_end;
-    const int span = o->mode == PDIT_MODE_PT ? std::min(o->exchange_period, se - o->sweep_begin) : se - o->sweep_begin;
-    return parts_of(o, p, span);
-}
-
 // Whether the workspace holds every replica's table (the table kernels: PT
 // segments and tables in global memory; `persist`: any kernel whose state is
 // kept between calls by the server, the dot kernel's permuted flow matrix;
 // either kernel's table between the parts of a launch).
 bool needs_tables(const pdit_opts *o, const Plan &p, bool persist = false) {
-    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem) || call_parts(o, p) > 1;
+    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem) || may_split(o, p);
 }
 
 Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base, bool persist = false) {
@@ -497,7 +499,7 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.queue = (int32_t *)take(4 * 64);
     w.status = (int32_t *)take(4);
     w.done = (int32_t *)take(4);
-    w.seg_done = call_parts(o, p) > 1 ? (int32_t *)take(4 * R) : nullptr;
+    w.seg_done = may_split(o, p) ? (int32_t *)take(4 * R) : nullptr;
     w.tables = needs_tables(o, p, persist) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
     w.bytes = off;
     return w;

@@ -339,3 +339,26 @@ def test_parallel_tempering_in_parts():
         r = O.anneal(D, F, ladder, S, 3, lo, hi, threads=L, mode="pt", ladder_len=L, period=4, timeout=2)
         check_equal(g, r, slice(lo, hi))
         assert np.array_equal(g["replica_rung"][lo:hi], r["rung"])
+
+
+def test_resume_from_a_whole_call_into_parts():
+    """A short call (too few sweeps to split) continued by a longer one that
+    is split into parts, on the first call's workspace: the workspace does not
+    depend on the sweep range, and the continuation equals one uninterrupted
+    oracle run."""
+    D, F = G.dense_instance(40, seed=29)
+    S, cut = 40, 6
+    beta = schedule(D, F, "linear", S)
+    p = P()
+    with p.Qap(D, F) as q:
+        p.pdit_set_class_update(q, False)
+        R = _slots(p, q) + 5
+        dbeta = torch.from_numpy(beta).cuda()
+        a = p.anneal_device(q, R, dbeta, S, 4, per_replica=True, sweep_end=cut)
+        b = p.anneal_device(q, R, dbeta, S, 4, per_replica=True, sweep_begin=cut, resume=True,
+                            workspace=a["workspace"])
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in b.items() if k != "workspace"}
+    for lo, hi in [(0, 2), (R - 2, R)]:
+        r = O.anneal(D, F, beta, S, 4, lo, hi, threads=2)
+        check_equal(g, r, slice(lo, hi))
