@@ -474,11 +474,14 @@ int parts_of(const pdit_opts *o, const Plan &p, int span) {
 // segments and tables in global memory; `persist`: any kernel whose state is
 // kept between calls by the server, the dot kernel's permuted flow matrix;
 // either kernel's table between the parts of a launch).
-bool needs_tables(const pdit_opts *o, const Plan &p, bool persist = false) {
-    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem) || may_split(o, p);
+bool needs_tables(const pdit_opts *o, const Plan &p, bool persist = false, bool whole = false) {
+    return persist || o->mode == PDIT_MODE_PT || (!p.dot && !p.tsmem) || (!whole && may_split(o, p));
 }
 
-Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base, bool persist = false) {
+// `whole`: the caller runs every launch as whole calls (no parts), so no
+// part counters or saved tables for them.
+Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base, bool persist = false,
+                bool whole = false) {
     const size_t R = (size_t)o->replicas, n = (size_t)h->n;
     size_t off = 0;
     Workspace w{};
@@ -499,8 +502,8 @@ Workspace carve(const pdit_qap *h, const pdit_opts *o, const Plan &p, char *base
     w.queue = (int32_t *)take(4 * 64);
     w.status = (int32_t *)take(4);
     w.done = (int32_t *)take(4);
-    w.seg_done = may_split(o, p) ? (int32_t *)take(4 * R) : nullptr;
-    w.tables = needs_tables(o, p, persist) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
+    w.seg_done = !whole && may_split(o, p) ? (int32_t *)take(4 * R) : nullptr;
+    w.tables = needs_tables(o, p, persist, whole) ? (int32_t *)take(4 * R * p.table_elems) : nullptr;
     w.bytes = off;
     return w;
 }
@@ -1368,12 +1371,12 @@ int pdit_anneal_noalloc(int n, const int32_t *D, const int32_t *F, int replicas,
     q.dD = q.dF = nullptr;  // not owned: nothing for ~pdit_qap to release
     if (rc) return rc;
     if (!plan.tsmem) return PDIT_ENOTSUP;
-    const Workspace need = carve(&q, &o, plan, nullptr);
+    const Workspace need = carve(&q, &o, plan, nullptr, false, true);  // whole calls only
     if (need.bytes > (size_t)PDIT_NOALLOC_SCRATCH_BYTES) return PDIT_ENOMEM;
     void *scratch = nullptr;
     rc = noalloc_scratch(&scratch);
     if (rc) return rc;
-    const Workspace w = carve(&q, &o, plan, (char *)scratch);
+    const Workspace w = carve(&q, &o, plan, (char *)scratch, false, true);
     cudaStream_t st = (cudaStream_t)stream;
     // The array keeps the previous call's contents: reset the status word
     // and the work counter; every replica's state is rewritten from scratch.
@@ -1639,7 +1642,7 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
         pdit_opts_init(&o);
         o.replicas = items[k].replicas;
         ws_off[k] = ws_total;
-        ws_total += align_up(carve(h, &o, plans[k], nullptr).bytes, kAlign);
+        ws_total += align_up(carve(h, &o, plans[k], nullptr, false, true).bytes, kAlign);  // batches: whole calls
     }
     // Shape classes.
     for (int k = 0; k < count; ++k) {
@@ -1680,7 +1683,7 @@ int pdit_batch_create(const pdit_batch_item *items, int count, uint32_t flags, p
         pdit_opts o;
         pdit_opts_init(&o);
         o.replicas = it.replicas;
-        const Workspace w = carve(h, &o, p, (char *)b->ws + ws_off[k]);
+        const Workspace w = carve(h, &o, p, (char *)b->ws + ws_off[k], false, true);
         pdit::SweepArgs &a = descs[k];
         a = pdit::SweepArgs{};
         fill_shape(a, h, p);
@@ -1896,7 +1899,7 @@ size_t request_footprint(const ServerRequest &r, const Plan &p) {
     pdit_opts o;
     pdit_opts_init(&o);
     o.replicas = r.replicas;
-    return carve(r.qap, &o, p, nullptr, true).bytes + (size_t)8 * r.n * r.n + 4 * (size_t)r.sweeps + 4 * r.n + 8 +
+    return carve(r.qap, &o, p, nullptr, true, true).bytes + (size_t)8 * r.n * r.n + 4 * (size_t)r.sweeps + 4 * r.n + 8 +
            1024;
 }
 
@@ -1919,7 +1922,7 @@ int admit(pdit_server *s, ServerRequest *r) {
     pdit_opts o;
     pdit_opts_init(&o);
     o.replicas = r->replicas;
-    const size_t wsb = carve(r->qap, &o, r->plan, nullptr, true).bytes;
+    const size_t wsb = carve(r->qap, &o, r->plan, nullptr, true, true).bytes;
     // stream-ordered allocations and copies on the upload stream (a copy from
     // pageable memory waits only for that stream's earlier work, none of
     // which is a kernel); the main stream waits for them before the next launch
@@ -1942,7 +1945,7 @@ int admit(pdit_server *s, ServerRequest *r) {
     if (e == cudaSuccess) e = cudaEventRecord(s->uploaded, up);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PDIT_ENOMEM : cuda_fail(e, "server admit");
     s->new_uploads = true;
-    r->w = carve(r->qap, &o, r->plan, (char *)r->ws, true);
+    r->w = carve(r->qap, &o, r->plan, (char *)r->ws, true, true);
     r->footprint = fp;
     s->used += fp;
     r->D.clear();
