@@ -176,12 +176,15 @@ __device__ __forceinline__ unsigned long long eq5_weight(int shifted_de, float b
     q = __fmaf_rn(q, y, 0.5f);
     q = __fmaf_rn(q, y, 1.0f);
     q = __fmaf_rn(q, y, 1.0f);
-    // q in (0.7, 1.5): a normal float; q = mant * 2^(exp - 150).
+    // q in (0.7, 1.5): a normal float, q = mant * 2^(exp - 150) with exp 126
+    // or 127, so w = trunc(q * 2^(53 - k)) = trunc(mant * 2^30 / 2^s) with
+    // s = 127 - exp + k in [0, 59] (k <= 58 for x <= 40): one 64-bit right
+    // shift of mant * 2^30 (< 2^54), exact for s <= 30 and the truncation
+    // otherwise; s = 63 gives the 0 of x > 40.
     const uint32_t bits = __float_as_uint(q);
-    const int sh = (int)(bits >> 23) - 150 + 53 - k;
-    const unsigned long long mant = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
-    const unsigned long long w = sh >= 0 ? (mant << sh) : (sh > -24 ? (mant >> (-sh)) : 0ull);
-    return live ? w : 0ull;
+    const unsigned long long m30 = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u) << 30;
+    const int s = live ? 127 - (int)(bits >> 23) + k : 63;
+    return m30 >> s;
 }
 
 __device__ __forceinline__ int warp_min(int v) {
