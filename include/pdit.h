@@ -311,11 +311,16 @@ void pdit_opts_init(pdit_opts *o);
  * The workspace holds every replica's state between calls (permutation,
  * energy, best-so-far, counters, and in PT mode the influence tables), so a
  * call with PDIT_FLAG_RESUME continues exactly where the previous one
- * stopped. With the dot-product kernel in anneal or fixed mode and more
- * replicas than the GPU holds at once (not a whole number of rounds), each
- * replica's sweeps run as up to 16 parts in one launch; the workspace then
- * also holds every replica's permuted flow matrix (about n * n bytes) and a
- * part counter (4 bytes). Results do not depend on the parts.
+ * stopped. With more replicas than the GPU holds at once (not a whole
+ * number of rounds), the dot-product kernel and the table kernels with
+ * tables in shared memory run each replica's sweeps as parts, separate work
+ * units of one launch, in every mode. The parts are up to 16 of 8 to 1000
+ * sweeps, or of one sweep per PT exchange period. The workspace then also
+ * holds every replica's table (the dot kernel's permuted flow matrix, about
+ * n * n bytes; an n x stride int32 influence table) and a 4-byte part
+ * counter, whatever the sweep range, so a resumed call over a longer range
+ * fits the workspace of the call before it. Results do not depend on the
+ * parts.
  */
 size_t pdit_workspace_bytes(const pdit_qap *h, const pdit_opts *o);
 
